@@ -1,0 +1,401 @@
+"""Throughput benchmark: bulk CG-D detection + CG-P precoding on GB300.
+
+Workload (one step): S slots of the 128-antenna, 16-user, 64-QAM uplink and
+downlink, each slot 1200 subcarriers x 14 OFDM symbols with the channel
+constant over the 14 symbols (one instance = one subcarrier, 14 right-hand
+sides), i.i.d. CN(0,1) channels, SNR 10 dB, K = 3 CG iterations, FP32. A step
+is one cg_detect over all S*1200 instances (matched filter, Gram, CG,
+approximate SINR tracker, max-log LLRs) and one cg_precode over the same
+channels (Gram, CG, q = H v). Inputs are drawn once, resident in HBM and
+larger than L2.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+B, U, QAM, R, NSC = 128, 16, 6, 14, 1200
+SNR_DB = 10.0
+KITER = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--slots", type=int, default=32, help="1200x14 slots per step")
+    ap.add_argument("--U", type=int, default=U)
+    ap.add_argument("--K", type=int, default=KITER)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+
+def detect_bytes_per_instance(Bn, Un, Rn, q):
+    """Algorithmic HBM bytes of one CG-D instance: H and Y read once; x_hat,
+    mu, rho, LLRs and the status word written once."""
+    return (Bn * Un + Rn * Bn) * 8 + Rn * Un * (8 + 4 + 4 + 4 * q) + 4
+
+
+def precode_bytes_per_instance(Bn, Un, Rn):
+    """Algorithmic HBM bytes of one CG-P instance: H and T read, q, ||q|| and
+    the status word written."""
+    return (Bn * Un + Rn * Un) * 8 + Rn * Bn * 8 + Rn * 4 + 4
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1404_0424_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name: str):
+    """dram bytes per launch recorded in profiles/<name>.md, if the kernel
+    sources have not changed since that capture."""
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    mh = re.search(r"kernel_source_hash:\s*(\w+)", txt)
+    mt = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not mh or not mt or mh.group(1) != kernel_source_hash():
+        return None
+    return float(mt.group(1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reported baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def time_oracle(seconds: float, Un: int, K: int):
+    import numpy as np
+
+    import oracle
+    from paper_1404_0424_gb300 import workload as wl
+    d = wl.uplink(B, Un, QAM, n=64, R=R, snr_db=SNR_DB, seed=7)
+    t0 = time.perf_counter()
+    solves = 0
+    inst = 0
+    while inst < 64:
+        oracle.cg_detect(d["H"][inst:inst + 1], d["Y"][inst:inst + 1], d["N0"], 1.0, K, QAM)
+        oracle.cg_precode(d["H"][inst:inst + 1], d["x"][inst:inst + 1], d["N0"], 1.0, K)
+        solves += 2 * R
+        inst += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    _ = np
+    return solves / dt, inst, dt
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1404_0424_gb300 import build, cabi, workload as wl
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cabi.library(build.build())
+
+    Un, K = args.U, args.K
+    n = args.slots * NSC
+    up = wl.uplink_torch(B, Un, QAM, n=n, R=R, snr_db=SNR_DB, seed=1000 + rank, device=dev)
+    H, Y, N0 = up["H"], up["Y"], up["N0"]
+    T = up["x"].contiguous()          # downlink symbols on the same channels
+    del up
+    xhat = torch.empty((n, R, Un), dtype=torch.complex64, device=dev)
+    mu = torch.empty((n, R, Un), dtype=torch.float32, device=dev)
+    rho = torch.empty_like(mu)
+    llr = torch.empty((n, R, Un, QAM), dtype=torch.float32, device=dev)
+    st = torch.empty((n,), dtype=torch.int32, device=dev)
+    q = torch.empty((n, R, B), dtype=torch.complex64, device=dev)
+    qn = torch.empty((n, R), dtype=torch.float32, device=dev)
+    stp = torch.empty((n,), dtype=torch.int32, device=dev)
+    p = cabi.params(B, Un, QAM, K, R, N0)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        rc = cabi.cg_detect(p, n, H, Y, xhat, mu, rho, llr, st, stream)
+        if evs is not None:
+            evs[1].record(stream)
+        rc |= cabi.cg_precode(p, n, H, T, q, qn, 0, stp, stream)
+        if evs is not None:
+            evs[2].record(stream)
+        if rc:
+            raise RuntimeError(cabi.cg_strerror(rc))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert int(st.abs().sum()) == 0 and int(stp.abs().sum()) == 0
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(evs[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    det_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    pre_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    ms_step = elapsed_ms / args.steps
+    solves_step = 2 * n * R * world
+    value = solves_step / (ms_step / 1e3)
+    llrs = n * R * Un * QAM * world / (ms_step / 1e3)
+
+    # plain per-call latency: one 1200 x 14 slot (detect + precode) per call
+    lat = []
+    Hs, Ys, Ts = H[:NSC], Y[:NSC], T[:NSC]
+    for i in range(60):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cabi.cg_detect(p, NSC, Hs, Ys, xhat, mu, rho, llr, st, stream)
+        cabi.cg_precode(p, NSC, Hs, Ts, q, qn, 0, stp, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= 10:
+            lat.append(e0.elapsed_time(e1))
+    lat.sort()
+
+    # end-to-end through the host-memory ABI (pinned buffers, copies timed)
+    e2e = None
+    if not args.no_e2e:
+        ne = min(n, 8 * NSC)
+        Hh = H[:ne].cpu().pin_memory()
+        Yh = Y[:ne].cpu().pin_memory()
+        Th = T[:ne].cpu().pin_memory()
+        ox = torch.empty((ne, R, Un), dtype=torch.complex64).pin_memory()
+        om = torch.empty((ne, R, Un), dtype=torch.float32).pin_memory()
+        orh = torch.empty_like(om).pin_memory()
+        ol = torch.empty((ne, R, Un, QAM), dtype=torch.float32).pin_memory()
+        os_ = torch.empty((ne,), dtype=torch.int32).pin_memory()
+        oq = torch.empty((ne, R, B), dtype=torch.complex64).pin_memory()
+        oqn = torch.empty((ne, R), dtype=torch.float32).pin_memory()
+        osp = torch.empty((ne,), dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            rc = cabi.cg_detect_host(p, ne, Hh, Yh, ox, om, orh, ol, os_, stream)
+            rc |= cabi.cg_precode_host(p, ne, Hh, Th, oq, oqn, 0, osp, stream)
+            if rc:
+                raise RuntimeError(cabi.cg_strerror(rc))
+
+        for _ in range(2):
+            e2e_step()
+        ke = max(3, args.steps // 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        dt = (time.perf_counter() - t0) / ke
+        h2d = ne * (B * Un + R * B) * 8 + ne * (B * Un + R * Un) * 8
+        d2h = ne * (detect_bytes_per_instance(B, Un, R, QAM) - (B * Un + R * B) * 8) + \
+            ne * (R * B * 8 + R * 4 + 4)
+        e2e = {"value": 2 * ne * R / dt, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "instances_per_step": ne}
+        cabi.cg_release_workspace()
+
+    peaks, peak_kind = measured_peaks()
+    det_bytes = detect_bytes_per_instance(B, Un, R, QAM) * n
+    achieved = det_bytes / (det_ms / 1e3) / 1e9
+    traffic = profiled_traffic(f"detect_fp32_{B}x{Un}")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": traffic, "kernel": "detect_kernel", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": det_bytes}
+    pre_bytes = precode_bytes_per_instance(B, Un, R) * n
+    pre_gbs = pre_bytes / (pre_ms / 1e3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, ninst, dt = time_oracle(args.cpu_seconds, Un, K)
+        cpu = {"value": rate, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"{ninst} subcarriers x {R} symbols, detect + precode, "
+                         f"{dt:.1f} s single-threaded numpy FP64"}
+
+    if rank == 0:
+        line = {
+            "metric": "CG solves/s (detect + precode) at B=128, U=16, 64-QAM, R=14, K=3",
+            "value": round(value, 1), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded i.i.d. CN(0,1) channels, Gray 64-QAM, AWGN at 10 dB)",
+            "config": {"workload": f"uplink CG-D + downlink CG-P, B={B}, U={Un}, 64-QAM, "
+                                   f"{NSC} subcarriers x {R} symbols per slot, K={K}, "
+                                   f"SNR {SNR_DB} dB, FP32",
+                       "slots_per_step": args.slots, "instances_per_step": n,
+                       "l2": "inputs larger than L2 (%.2f GB read per step)" %
+                             ((det_bytes + pre_bytes) / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "llrs_per_s": round(llrs, 1),
+            "detect_solves_per_s": round(n * R * world / (det_ms / 1e3), 1),
+            "precode_solves_per_s": round(n * R * world / (pre_ms / 1e3), 1),
+            "detect_ms": round(det_ms, 4), "precode_ms": round(pre_ms, 4),
+            "precode_gbs": round(pre_gbs, 1),
+            "latency_ms": {"plain_slot_p50": round(lat[len(lat) // 2], 4),
+                           "plain_slot_p99": round(lat[min(len(lat) - 1,
+                                                           int(0.99 * len(lat)))], 4),
+                           "what": "one 1200x14 slot, detect + precode, one launch each"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": ck,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    _ = np, math
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    Un, K = args.U, args.K
+    per = []
+    warm = max(args.warmup, 3)
+    budget = max(1.0, 120.0 / (args.steps + warm))
+    for s in range(args.steps + warm):
+        rate, ninst, dt = time_oracle(budget, Un, K)
+        if s >= warm:
+            per.append((rate, ninst, dt))
+    rate = sum(r[1] for r in per) * 2 * R / sum(r[2] for r in per)
+    line = {
+        "impl": "reference",
+        "metric": "CG solves/s (detect + precode) at B=128, U=16, 64-QAM, R=14, K=3",
+        "value": round(rate, 2), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": warm, "ms_per_step": round(1e3 * sum(r[2] for r in per) / len(per), 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded i.i.d. CN(0,1) channels, Gray 64-QAM, AWGN at 10 dB)",
+        "config": {"workload": f"uplink CG-D + downlink CG-P, B={B}, U={Un}, 64-QAM, "
+                               f"{NSC} subcarriers x {R} symbols per slot, K={K}, "
+                               f"SNR {SNR_DB} dB", "parallelism": "host, 1 thread"},
+        "cpu_baseline": {"value": round(rate, 2), "unit": "solves/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"each step: subcarriers for {budget:.1f} s of FP64 numpy"},
+        "e2e": {"value": round(rate, 2), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,149 @@
+/*
+ * cgmimo.h - C ABI of libcgmimo: conjugate-gradient (CG) soft-output MMSE
+ * detection and CG precoding for massive MIMO on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is Algorithm 1 of Yin, Wu, Cavallaro and Studer, "Conjugate
+ * Gradient-based Soft-Output Detection and Precoding in Massive MIMO Systems"
+ * (arXiv 1404.0424), run in bulk: one CG solve per (instance, right-hand
+ * side). An instance is one subcarrier: a channel H shared by R right-hand
+ * sides (OFDM symbols).
+ *
+ * Data layout (row-major, no padding, little-endian):
+ *   complex values are complex64: interleaved (re, im) float32 pairs;
+ *   H      [n][B][U]  uplink channel H_u of Eq. 1 (the downlink uses H_d = H_u^H);
+ *   Y      [n][R][B]  receive vectors y of Eq. 1;
+ *   T      [n][R][U]  precoder input symbols t of Eq. 5;
+ *   xhat   [n][R][U]  x_hat_K = v_K (Algorithm 1, detection output);
+ *   mu,rho [n][R][U]  float32 mu_{i|K}, rho_{i|K} (Sec. III-C);
+ *   llr    [n][R][U][qam_bits] float32 max-log LLRs of Eq. 4, bit b_0 first;
+ *   q      [n][R][B]  precoded vectors q_K = H_d^H v_K (Algorithm 1, precoding output);
+ *   qnorm  [n][R]     float32 ||q_K||_2;
+ *   status [n]        int32 bitwise OR of CG_STATUS_* over the instance's right-hand sides.
+ *
+ * Constellation: square Gray QAM with E|x|^2 = Es. Bits b_0..b_{q/2-1} pick
+ * the in-phase level and b_{q/2}..b_{q-1} the quadrature level, each read
+ * MSB-first as the Gray code j ^ (j >> 1) of the level index j; level j is
+ * (2j - (L-1)) c sqrt(Es) with L = 2^(q/2) and c = sqrt(3 / (2 (M - 1))).
+ * LLR sign follows Eq. 4 as printed: L > 0 favours bit 1.
+ *
+ * Memory and streams: every pointer argument of cg_detect / cg_precode is a
+ * DEVICE pointer owned by the caller; the library keeps no reference after
+ * the call returns. Work is enqueued asynchronously on `stream` (a
+ * cudaStream_t; NULL is the legacy default stream) on the current device.
+ * The *_host variants take HOST pointers (pinned memory gives the best
+ * bandwidth), stage through a library-owned device workspace and return
+ * after the results are back in host memory.
+ *
+ * Errors: functions return CG_OK (0) or a negative CG_E* code and enqueue no
+ * work on error; cg_strerror() names the code. Argument checks happen on the
+ * host before any CUDA call. Per-instance numerical conditions are reported
+ * in `status`, never as a return code.
+ */
+#ifndef CGMIMO_H
+#define CGMIMO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define CG_OK 0
+#define CG_EINVAL (-1)     /* invalid argument (size, mode, pointer or alignment) */
+#define CG_ECUDA (-2)      /* a CUDA runtime call or kernel launch failed */
+#define CG_ENOMEM (-3)     /* device or pinned-host allocation failed */
+#define CG_EAGAIN (-4)     /* resource temporarily full (serving queue) */
+#define CG_ETIMEDOUT (-5)  /* a bounded wait expired */
+#define CG_ENOTSUP (-6)    /* valid but unsupported combination of modes */
+
+/* Per-instance status bits. */
+#define CG_STATUS_BREAKDOWN 1  /* CG stopped before K: ||r_{k-1}||^2 or Re(p^H A p) not > 0 */
+#define CG_STATUS_MU_NONPOS 2  /* some mu_{i|K} <= 0: that user's LLRs are set to 0 */
+#define CG_STATUS_TIMEOUT 4    /* an input copy did not complete in time; outputs not written */
+
+/* SINR tracker (Sec. III-C). */
+#define CG_SINR_APPROX 0  /* Eqs. 11-13: diagonal recursion, rho = G_ii / N0 */
+#define CG_SINR_EXACT 1   /* Eq. 10 and the B = L_K G, C = B L_K^H expressions */
+
+/* How e = A p is formed inside Algorithm 1 (line 9). */
+#define CG_AMUL_AUTO 0      /* library choice */
+#define CG_AMUL_EXPLICIT 1  /* form A = H^H H + (N0/Es) I once per instance */
+#define CG_AMUL_IMPLICIT 2  /* e = H^H (H p) + (N0/Es) p, two matrix-vector products */
+
+/* Arithmetic of the Gram H^H H and matched filter H^H y (CG itself is FP32). */
+#define CG_PREC_FP32 0
+#define CG_PREC_BF16 1    /* one BF16 tensor-core pass, FP32 accumulate */
+#define CG_PREC_FP16 2    /* one FP16 tensor-core pass, FP32 accumulate */
+#define CG_PREC_BF16X3 3  /* hi+lo split BF16, three tensor-core passes */
+#define CG_PREC_FP16X3 4  /* hi+lo split FP16, three tensor-core passes */
+
+/* Size limits of one call. */
+#define CG_U_MAX 32
+#define CG_B_MAX 256
+#define CG_R_MAX 16
+#define CG_K_MAX 32
+
+/* Problem description shared by every instance of one call.
+ *   B         base-station antennas, U <= B <= CG_B_MAX (Sec. II)
+ *   U         users, 1 <= U <= CG_U_MAX
+ *   qam_bits  bits per symbol q, one of 2, 4, 6, 8 (QPSK..256-QAM)
+ *   K         CG iterations, 1 <= K <= U (CG is exact at K = U, Sec. III-B)
+ *   R         right-hand sides per instance, 1 <= R <= CG_R_MAX
+ *   N0, Es    noise variance and symbol energy, finite and > 0; the
+ *             regulariser is N0/Es (rho_u^-1 of Eq. 2, rho_d^-1 of Eq. 6)
+ *   sinr_mode CG_SINR_*; amul_mode CG_AMUL_*; precision CG_PREC_*          */
+typedef struct cg_params {
+  int32_t B, U, qam_bits, K, R;
+  float N0, Es;
+  int32_t sinr_mode;
+  int32_t amul_mode;
+  int32_t precision;
+} cg_params;
+
+/* CG-D soft-output detection (Sec. III-B, Algorithm 1 with lines 15-16):
+ * b = H^H y, A = H^H H + (N0/Es) I, K CG iterations, the chosen SINR tracker,
+ * then x_hat, mu, rho and max-log LLRs (Eq. 4). H and Y must be 8-byte
+ * aligned; any of xhat, mu, rho, llr, status may be NULL (not written).
+ * n_inst = 0 is a no-op. */
+int cg_detect(const cg_params* p, int64_t n_inst, const void* H, const void* Y,
+              void* xhat, float* mu, float* rho, float* llr, int32_t* status,
+              void* stream);
+
+/* CG-P precoding (Sec. III-D): b = t, A = H_d H_d^H + (N0/Es) I with
+ * H_d = H_u^H, K CG iterations, q = H_d^H v_K (Algorithm 1 line 20).
+ * With normalize != 0 the power-normalised s = q / ||q||_2 (Sec. II-B) is
+ * written to q instead. qnorm and status may be NULL. The sinr_mode and
+ * qam_bits fields are ignored. */
+int cg_precode(const cg_params* p, int64_t n_inst, const void* H, const void* T,
+               void* q, float* qnorm, int32_t normalize, int32_t* status,
+               void* stream);
+
+/* Host-memory variants of the two calls above: same arguments and layouts,
+ * but every array is in HOST memory. Inputs are copied in chunks to a
+ * device workspace owned by the library (allocated on first use, grown as
+ * needed, freed by cg_release_workspace), processed, and copied back;
+ * copies of one chunk overlap the compute of the next. Blocking: returns
+ * once all outputs are in host memory. `stream` orders the work after
+ * earlier work on that stream. */
+int cg_detect_host(const cg_params* p, int64_t n_inst, const void* H, const void* Y,
+                   void* xhat, float* mu, float* rho, float* llr, int32_t* status,
+                   void* stream);
+int cg_precode_host(const cg_params* p, int64_t n_inst, const void* H, const void* T,
+                    void* q, float* qnorm, int32_t normalize, int32_t* status,
+                    void* stream);
+
+/* Frees the workspace of the *_host calls on the current device. */
+int cg_release_workspace(void);
+
+/* Human-readable name of a CG_* return code (static string, never NULL). */
+const char* cg_strerror(int code);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int cg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CGMIMO_H */

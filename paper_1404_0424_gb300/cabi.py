@@ -1,0 +1,200 @@
+"""Thin ctypes binding of libcgmimo (include/cgmimo.h).
+
+The functions cg_detect, cg_precode, cg_detect_host, cg_precode_host,
+cg_release_workspace, cg_strerror and cg_version have the names and argument
+order of the C ABI. detect() and precode() are conveniences that allocate the
+outputs as torch tensors and marshal pointers; every step of the computation
+runs in the CUDA library. There is no fallback: if the library is missing
+the first call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+HEADER = os.path.join(_ROOT, "include", "cgmimo.h")
+LIB_PATH = os.path.join(_PKG, "_build", "libcgmimo.so")
+
+
+def _header_constants(path: str = HEADER) -> dict:
+    consts = {}
+    with open(path) as f:
+        for m in re.finditer(r"^#define\s+(CG_\w+)\s+\(?(-?\d+)\)?", f.read(), re.M):
+            consts[m.group(1)] = int(m.group(2))
+    return consts
+
+
+C = _header_constants()
+globals().update(C)
+
+
+class CgParams(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int32), ("U", ctypes.c_int32), ("qam_bits", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("R", ctypes.c_int32), ("N0", ctypes.c_float),
+                ("Es", ctypes.c_float), ("sinr_mode", ctypes.c_int32),
+                ("amul_mode", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class CgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {cg_strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_FP = ctypes.POINTER(ctypes.c_float)
+_IP = ctypes.POINTER(ctypes.c_int32)
+
+_SIGS = {
+    "cg_detect": [ctypes.POINTER(CgParams), ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                  _VP],
+    "cg_precode": [ctypes.POINTER(CgParams), ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_int32,
+                   _VP, _VP],
+    "cg_detect_host": [ctypes.POINTER(CgParams), ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP,
+                       _VP, _VP],
+    "cg_precode_host": [ctypes.POINTER(CgParams), ctypes.c_int64, _VP, _VP, _VP, _VP,
+                        ctypes.c_int32, _VP, _VP],
+    "cg_release_workspace": [],
+    "cg_strerror": [ctypes.c_int],
+    "cg_version": [],
+}
+
+
+def library(path: str | None = None) -> ctypes.CDLL:
+    """Loads libcgmimo.so once (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise OSError(f"libcgmimo.so not found at {p}; run paper_1404_0424_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        for name, args in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_char_p if name == "cg_strerror" else ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):          # numpy array (host)
+        return t.ctypes.data
+    return int(t)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # noqa: BLE001
+            return None
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def params(B, U, qam_bits, K, R, N0, Es=1.0, sinr_mode=0, amul_mode=0, precision=0) -> CgParams:
+    return CgParams(int(B), int(U), int(qam_bits), int(K), int(R), float(N0), float(Es),
+                    int(sinr_mode), int(amul_mode), int(precision))
+
+
+# ---------------------------------------------------------------------------
+# C ABI, same names
+# ---------------------------------------------------------------------------
+
+def cg_strerror(code: int) -> str:
+    return library().cg_strerror(int(code)).decode()
+
+
+def cg_version() -> int:
+    return library().cg_version()
+
+
+def cg_release_workspace() -> int:
+    return library().cg_release_workspace()
+
+
+def cg_detect(p: CgParams, n_inst, H, Y, xhat=None, mu=None, rho=None, llr=None, status=None,
+              stream=None) -> int:
+    return library().cg_detect(ctypes.byref(p), int(n_inst), _ptr(H), _ptr(Y), _ptr(xhat),
+                               _ptr(mu), _ptr(rho), _ptr(llr), _ptr(status), _stream(stream))
+
+
+def cg_precode(p: CgParams, n_inst, H, T, q, qnorm=None, normalize=0, status=None,
+               stream=None) -> int:
+    return library().cg_precode(ctypes.byref(p), int(n_inst), _ptr(H), _ptr(T), _ptr(q),
+                                _ptr(qnorm), int(normalize), _ptr(status), _stream(stream))
+
+
+def cg_detect_host(p: CgParams, n_inst, H, Y, xhat=None, mu=None, rho=None, llr=None,
+                   status=None, stream=None) -> int:
+    return library().cg_detect_host(ctypes.byref(p), int(n_inst), _ptr(H), _ptr(Y), _ptr(xhat),
+                                    _ptr(mu), _ptr(rho), _ptr(llr), _ptr(status),
+                                    _stream(stream))
+
+
+def cg_precode_host(p: CgParams, n_inst, H, T, q, qnorm=None, normalize=0, status=None,
+                    stream=None) -> int:
+    return library().cg_precode_host(ctypes.byref(p), int(n_inst), _ptr(H), _ptr(T), _ptr(q),
+                                     _ptr(qnorm), int(normalize), _ptr(status), _stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# Conveniences over torch tensors (allocation and pointer marshalling only)
+# ---------------------------------------------------------------------------
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise CgError(rc, where)
+
+
+def detect(H, Y, N0, K, qam_bits, Es=1.0, sinr_mode=0, amul_mode=0, precision=0,
+           outputs=("xhat", "mu", "rho", "llr", "status"), stream=None) -> dict:
+    """CG-D on device tensors H[n, B, U], Y[n, R, B] (complex64, contiguous)."""
+    import torch
+    n, B, U = H.shape
+    R = Y.shape[1]
+    assert Y.shape == (n, R, B) and H.is_contiguous() and Y.is_contiguous()
+    assert H.dtype == torch.complex64 and Y.dtype == torch.complex64
+    dev = H.device
+    out = {}
+    if "xhat" in outputs:
+        out["xhat"] = torch.empty((n, R, U), dtype=torch.complex64, device=dev)
+    if "mu" in outputs:
+        out["mu"] = torch.empty((n, R, U), dtype=torch.float32, device=dev)
+    if "rho" in outputs:
+        out["rho"] = torch.empty((n, R, U), dtype=torch.float32, device=dev)
+    if "llr" in outputs:
+        out["llr"] = torch.empty((n, R, U, qam_bits), dtype=torch.float32, device=dev)
+    if "status" in outputs:
+        out["status"] = torch.empty((n,), dtype=torch.int32, device=dev)
+    p = params(B, U, qam_bits, K, R, N0, Es, sinr_mode, amul_mode, precision)
+    _check(cg_detect(p, n, H, Y, out.get("xhat"), out.get("mu"), out.get("rho"), out.get("llr"),
+                     out.get("status"), stream), "cg_detect")
+    return out
+
+
+def precode(H, T, N0, K, Es=1.0, normalize=False, amul_mode=0, precision=0, stream=None) -> dict:
+    """CG-P on device tensors H[n, B, U], T[n, R, U] (complex64, contiguous)."""
+    import torch
+    n, B, U = H.shape
+    R = T.shape[1]
+    assert T.shape == (n, R, U) and H.is_contiguous() and T.is_contiguous()
+    dev = H.device
+    out = {"q": torch.empty((n, R, B), dtype=torch.complex64, device=dev),
+           "qnorm": torch.empty((n, R), dtype=torch.float32, device=dev),
+           "status": torch.empty((n,), dtype=torch.int32, device=dev)}
+    p = params(B, U, 2, K, R, N0, Es, 0, amul_mode, precision)
+    _check(cg_precode(p, n, H, T, out["q"], out["qnorm"], int(bool(normalize)), out["status"],
+                      stream), "cg_precode")
+    return out

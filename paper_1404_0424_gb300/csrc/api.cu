@@ -1,0 +1,346 @@
+// C ABI of libcgmimo: argument validation, dispatch to the fused kernels,
+// and the chunked host-memory variants.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "cgmimo.h"
+#include "launch.cuh"
+
+namespace cgm {
+
+namespace {
+std::mutex g_dev_mu;
+DeviceInfo g_dev[64];
+bool g_dev_ok[64] = {false};
+}  // namespace
+
+int device_info(DeviceInfo* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (!g_dev_ok[dev]) {
+    DeviceInfo d;
+    if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return -1;
+    if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+      return -1;
+    g_dev[dev] = d;
+    g_dev_ok[dev] = true;
+  }
+  *out = g_dev[dev];
+  return 0;
+}
+
+}  // namespace cgm
+
+using namespace cgm;
+
+namespace {
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int check_common(const cg_params* p, int64_t n_inst) {
+  if (p == nullptr || n_inst < 0) return CG_EINVAL;
+  if (p->U < 1 || p->U > CG_U_MAX) return CG_EINVAL;
+  if (p->B < p->U || p->B > CG_B_MAX) return CG_EINVAL;
+  if (p->R < 1 || p->R > CG_R_MAX) return CG_EINVAL;
+  if (p->K < 1 || p->K > p->U || p->K > CG_K_MAX) return CG_EINVAL;
+  if (!(p->N0 > 0.f) || !std::isfinite(p->N0)) return CG_EINVAL;
+  if (!(p->Es > 0.f) || !std::isfinite(p->Es)) return CG_EINVAL;
+  if (p->amul_mode < CG_AMUL_AUTO || p->amul_mode > CG_AMUL_IMPLICIT) return CG_EINVAL;
+  if (p->precision < CG_PREC_FP32 || p->precision > CG_PREC_FP16X3) return CG_EINVAL;
+  return CG_OK;
+}
+
+int check_detect(const cg_params* p, int64_t n_inst, const void* H, const void* Y,
+                 const void* xhat, const float* mu, const float* rho, const float* llr,
+                 const int32_t* status) {
+  int rc = check_common(p, n_inst);
+  if (rc != CG_OK) return rc;
+  if (p->qam_bits != 2 && p->qam_bits != 4 && p->qam_bits != 6 && p->qam_bits != 8)
+    return CG_EINVAL;
+  if (p->sinr_mode != CG_SINR_APPROX && p->sinr_mode != CG_SINR_EXACT) return CG_EINVAL;
+  if (n_inst == 0) return CG_OK;
+  if (H == nullptr || Y == nullptr) return CG_EINVAL;
+  if (!aligned(H, 8) || !aligned(Y, 8) || !aligned(xhat, 8) || !aligned(mu, 4) ||
+      !aligned(rho, 4) || !aligned(llr, 8) || !aligned(status, 4))
+    return CG_EINVAL;
+  return CG_OK;
+}
+
+int check_precode(const cg_params* p, int64_t n_inst, const void* H, const void* T,
+                  const void* q, const float* qnorm, const int32_t* status) {
+  int rc = check_common(p, n_inst);
+  if (rc != CG_OK) return rc;
+  if (n_inst == 0) return CG_OK;
+  if (H == nullptr || T == nullptr || q == nullptr) return CG_EINVAL;
+  if (!aligned(H, 8) || !aligned(T, 8) || !aligned(q, 8) || !aligned(qnorm, 4) ||
+      !aligned(status, 4))
+    return CG_EINVAL;
+  return CG_OK;
+}
+
+// Modes implemented by the FP32 kernels of this build.
+int check_supported(const cg_params* p) {
+  if (p->precision != CG_PREC_FP32) return CG_ENOTSUP;
+  if (p->amul_mode == CG_AMUL_IMPLICIT) return CG_ENOTSUP;
+  return CG_OK;
+}
+
+int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void* Y, void* xhat,
+                  float* mu, float* rho, float* llr, int32_t* status, cudaStream_t s) {
+  DetectArgs a{};
+  a.H = static_cast<const float2*>(H);
+  a.Y = static_cast<const float2*>(Y);
+  a.xhat = static_cast<float2*>(xhat);
+  a.mu = mu;
+  a.rho = rho;
+  a.llr = llr;
+  a.status = status;
+  a.n_inst = n_inst;
+  a.B = p->B;
+  a.U = p->U;
+  a.R = p->R;
+  a.K = p->K;
+  a.q = p->qam_bits;
+  a.N0 = p->N0;
+  a.Es = p->Es;
+  a.sigma = p->N0 / p->Es;
+  a.exact = p->sinr_mode == CG_SINR_EXACT;
+  a.bulk = (p->B % 2 == 0) && aligned(H, 16) && aligned(Y, 16);
+  const cudaError_t err = launch_detect(padded_users(p->U), a, s, nullptr);
+  if (err == cudaErrorInvalidValue) return CG_EINVAL;
+  return err == cudaSuccess ? CG_OK : CG_ECUDA;
+}
+
+int precode_device(const cg_params* p, int64_t n_inst, const void* H, const void* T, void* q,
+                   float* qnorm, int32_t normalize, int32_t* status, cudaStream_t s) {
+  PrecodeArgs a{};
+  a.H = static_cast<const float2*>(H);
+  a.T = static_cast<const float2*>(T);
+  a.q = static_cast<float2*>(q);
+  a.qnorm = qnorm;
+  a.status = status;
+  a.n_inst = n_inst;
+  a.B = p->B;
+  a.U = p->U;
+  a.R = p->R;
+  a.K = p->K;
+  a.sigma = p->N0 / p->Es;
+  a.normalize = normalize != 0;
+  a.bulk_h = ((p->B * p->U) % 2 == 0) && aligned(H, 16);
+  a.bulk_t = ((p->R * p->U) % 2 == 0) && aligned(T, 16);
+  const cudaError_t err = launch_precode(padded_users(p->U), a, s, nullptr);
+  if (err == cudaErrorInvalidValue) return CG_EINVAL;
+  return err == cudaSuccess ? CG_OK : CG_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace of the host-memory variants: one device buffer and two streams
+// per device, used by one call at a time.
+// ---------------------------------------------------------------------------
+
+struct HostWorkspace {
+  void* d = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaEvent_t ready = nullptr;
+};
+
+std::mutex g_ws_mu;
+HostWorkspace g_ws[64];
+
+constexpr size_t kChunkBytes = size_t(64) << 20;  // inputs + outputs of one chunk
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int workspace_acquire(size_t need, HostWorkspace** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CG_ECUDA;
+  HostWorkspace& w = g_ws[dev];
+  if (w.st[0] == nullptr) {
+    for (int i = 0; i < 2; ++i)
+      if (cudaStreamCreateWithFlags(&w.st[i], cudaStreamNonBlocking) != cudaSuccess)
+        return CG_ECUDA;
+    if (cudaEventCreateWithFlags(&w.ready, cudaEventDisableTiming) != cudaSuccess)
+      return CG_ECUDA;
+  }
+  if (w.bytes < need) {
+    if (w.d != nullptr) cudaFree(w.d);
+    w.d = nullptr;
+    w.bytes = 0;
+    if (cudaMalloc(&w.d, need) != cudaSuccess) return CG_ENOMEM;
+    w.bytes = need;
+  }
+  *out = &w;
+  return CG_OK;
+}
+
+// Makes the workspace streams wait for earlier work on the caller's stream.
+int order_after(HostWorkspace* w, cudaStream_t user) {
+  if (cudaEventRecord(w->ready, user) != cudaSuccess) return CG_ECUDA;
+  for (int i = 0; i < 2; ++i)
+    if (cudaStreamWaitEvent(w->st[i], w->ready, 0) != cudaSuccess) return CG_ECUDA;
+  return CG_OK;
+}
+
+int finish(HostWorkspace* w, int rc) {
+  for (int i = 0; i < 2; ++i)
+    if (cudaStreamSynchronize(w->st[i]) != cudaSuccess && rc == CG_OK) rc = CG_ECUDA;
+  return rc;
+}
+
+cudaError_t h2d(void* dst, const void* src, size_t n, cudaStream_t s) {
+  return n ? cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s) : cudaSuccess;
+}
+
+cudaError_t d2h(void* dst, const void* src, size_t n, cudaStream_t s) {
+  return n ? cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cg_detect(const cg_params* p, int64_t n_inst, const void* H, const void* Y, void* xhat,
+              float* mu, float* rho, float* llr, int32_t* status, void* stream) {
+  int rc = check_detect(p, n_inst, H, Y, xhat, mu, rho, llr, status);
+  if (rc != CG_OK || n_inst == 0) return rc;
+  if ((rc = check_supported(p)) != CG_OK) return rc;
+  return detect_device(p, n_inst, H, Y, xhat, mu, rho, llr, status,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int cg_precode(const cg_params* p, int64_t n_inst, const void* H, const void* T, void* q,
+               float* qnorm, int32_t normalize, int32_t* status, void* stream) {
+  int rc = check_precode(p, n_inst, H, T, q, qnorm, status);
+  if (rc != CG_OK || n_inst == 0) return rc;
+  if ((rc = check_supported(p)) != CG_OK) return rc;
+  return precode_device(p, n_inst, H, T, q, qnorm, normalize, status,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int cg_detect_host(const cg_params* p, int64_t n_inst, const void* H, const void* Y, void* xhat,
+                   float* mu, float* rho, float* llr, int32_t* status, void* stream) {
+  int rc = check_detect(p, n_inst, H, Y, xhat, mu, rho, llr, status);
+  if (rc != CG_OK || n_inst == 0) return rc;
+  if ((rc = check_supported(p)) != CG_OK) return rc;
+  const size_t B = p->B, U = p->U, R = p->R, q = p->qam_bits;
+  const size_t bH = B * U * 8, bY = R * B * 8;
+  const size_t bX = xhat ? R * U * 8 : 0, bM = mu ? R * U * 4 : 0, bR = rho ? R * U * 4 : 0;
+  const size_t bL = llr ? R * U * q * 4 : 0, bS = status ? 4 : 0;
+  const size_t per = bH + bY + bX + bM + bR + bL + bS;
+  int64_t chunk = int64_t(kChunkBytes / per);
+  if (chunk < 1) chunk = 1;
+  if (chunk > n_inst) chunk = n_inst;
+  const size_t c = size_t(chunk);
+  const size_t oH = 0, oY = up256(oH + c * bH), oX = up256(oY + c * bY), oM = up256(oX + c * bX);
+  const size_t oR = up256(oM + c * bM), oL = up256(oR + c * bR), oS = up256(oL + c * bL);
+  const size_t set = up256(oS + c * bS);
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  HostWorkspace* w = nullptr;
+  if ((rc = workspace_acquire(2 * set, &w)) != CG_OK) return rc;
+  if ((rc = order_after(w, static_cast<cudaStream_t>(stream))) != CG_OK) return rc;
+  const char* hH = static_cast<const char*>(H);
+  const char* hY = static_cast<const char*>(Y);
+  int k = 0;
+  for (int64_t off = 0; off < n_inst && rc == CG_OK; off += chunk, ++k) {
+    const size_t nc = size_t(n_inst - off < chunk ? n_inst - off : chunk);
+    cudaStream_t s = w->st[k & 1];
+    char* base = static_cast<char*>(w->d) + (k & 1) * set;
+    if (h2d(base + oH, hH + off * bH, nc * bH, s) != cudaSuccess ||
+        h2d(base + oY, hY + off * bY, nc * bY, s) != cudaSuccess) {
+      rc = CG_ECUDA;
+      break;
+    }
+    rc = detect_device(p, int64_t(nc), base + oH, base + oY, xhat ? base + oX : nullptr,
+                       mu ? reinterpret_cast<float*>(base + oM) : nullptr,
+                       rho ? reinterpret_cast<float*>(base + oR) : nullptr,
+                       llr ? reinterpret_cast<float*>(base + oL) : nullptr,
+                       status ? reinterpret_cast<int32_t*>(base + oS) : nullptr, s);
+    if (rc != CG_OK) break;
+    if (d2h(static_cast<char*>(xhat) + off * bX, base + oX, nc * bX, s) != cudaSuccess ||
+        d2h(reinterpret_cast<char*>(mu) + off * bM, base + oM, nc * bM, s) != cudaSuccess ||
+        d2h(reinterpret_cast<char*>(rho) + off * bR, base + oR, nc * bR, s) != cudaSuccess ||
+        d2h(reinterpret_cast<char*>(llr) + off * bL, base + oL, nc * bL, s) != cudaSuccess ||
+        d2h(reinterpret_cast<char*>(status) + off * bS, base + oS, nc * bS, s) != cudaSuccess)
+      rc = CG_ECUDA;
+  }
+  return finish(w, rc);
+}
+
+int cg_precode_host(const cg_params* p, int64_t n_inst, const void* H, const void* T, void* q,
+                    float* qnorm, int32_t normalize, int32_t* status, void* stream) {
+  int rc = check_precode(p, n_inst, H, T, q, qnorm, status);
+  if (rc != CG_OK || n_inst == 0) return rc;
+  if ((rc = check_supported(p)) != CG_OK) return rc;
+  const size_t B = p->B, U = p->U, R = p->R;
+  const size_t bH = B * U * 8, bT = R * U * 8, bQ = R * B * 8;
+  const size_t bN = qnorm ? R * 4 : 0, bS = status ? 4 : 0;
+  const size_t per = bH + bT + bQ + bN + bS;
+  int64_t chunk = int64_t(kChunkBytes / per);
+  if (chunk < 1) chunk = 1;
+  if (chunk > n_inst) chunk = n_inst;
+  const size_t c = size_t(chunk);
+  const size_t oH = 0, oT = up256(oH + c * bH), oQ = up256(oT + c * bT), oN = up256(oQ + c * bQ);
+  const size_t oS = up256(oN + c * bN);
+  const size_t set = up256(oS + c * bS);
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  HostWorkspace* w = nullptr;
+  if ((rc = workspace_acquire(2 * set, &w)) != CG_OK) return rc;
+  if ((rc = order_after(w, static_cast<cudaStream_t>(stream))) != CG_OK) return rc;
+  const char* hH = static_cast<const char*>(H);
+  const char* hT = static_cast<const char*>(T);
+  int k = 0;
+  for (int64_t off = 0; off < n_inst && rc == CG_OK; off += chunk, ++k) {
+    const size_t nc = size_t(n_inst - off < chunk ? n_inst - off : chunk);
+    cudaStream_t s = w->st[k & 1];
+    char* base = static_cast<char*>(w->d) + (k & 1) * set;
+    if (h2d(base + oH, hH + off * bH, nc * bH, s) != cudaSuccess ||
+        h2d(base + oT, hT + off * bT, nc * bT, s) != cudaSuccess) {
+      rc = CG_ECUDA;
+      break;
+    }
+    rc = precode_device(p, int64_t(nc), base + oH, base + oT, base + oQ,
+                        qnorm ? reinterpret_cast<float*>(base + oN) : nullptr, normalize,
+                        status ? reinterpret_cast<int32_t*>(base + oS) : nullptr, s);
+    if (rc != CG_OK) break;
+    if (d2h(static_cast<char*>(q) + off * bQ, base + oQ, nc * bQ, s) != cudaSuccess ||
+        d2h(reinterpret_cast<char*>(qnorm) + off * bN, base + oN, nc * bN, s) != cudaSuccess ||
+        d2h(reinterpret_cast<char*>(status) + off * bS, base + oS, nc * bS, s) != cudaSuccess)
+      rc = CG_ECUDA;
+  }
+  return finish(w, rc);
+}
+
+int cg_release_workspace(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CG_ECUDA;
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  HostWorkspace& w = g_ws[dev];
+  int rc = CG_OK;
+  if (w.d != nullptr && cudaFree(w.d) != cudaSuccess) rc = CG_ECUDA;
+  w.d = nullptr;
+  w.bytes = 0;
+  return rc;
+}
+
+const char* cg_strerror(int code) {
+  switch (code) {
+    case CG_OK: return "CG_OK: success";
+    case CG_EINVAL: return "CG_EINVAL: invalid argument";
+    case CG_ECUDA: return "CG_ECUDA: CUDA runtime error";
+    case CG_ENOMEM: return "CG_ENOMEM: out of memory";
+    case CG_EAGAIN: return "CG_EAGAIN: resource temporarily full";
+    case CG_ETIMEDOUT: return "CG_ETIMEDOUT: bounded wait expired";
+    case CG_ENOTSUP: return "CG_ENOTSUP: unsupported mode combination";
+    default: return "unknown cgmimo error code";
+  }
+}
+
+int cg_version(void) { return 100; }
+
+}  // extern "C"

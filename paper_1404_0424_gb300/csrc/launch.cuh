@@ -1,0 +1,30 @@
+// Host-side launch helpers shared by the translation units of libcgmimo.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cg_kernels.cuh"
+
+namespace cgm {
+
+// Padded user count of the kernel instantiation that serves U users.
+inline int padded_users(int U) { return U <= 4 ? 4 : U <= 8 ? 8 : U <= 16 ? 16 : 32; }
+
+// Per-device facts the launchers need (cached; thread-safe).
+struct DeviceInfo {
+  int sm_count = 0;
+  int smem_optin = 0;
+};
+int device_info(DeviceInfo* out);
+
+// Launchers (defined in detect.cu / precode.cu). Return cudaError_t values.
+cudaError_t launch_detect(int UT, const DetectArgs& a, cudaStream_t s, int* grid_out);
+cudaError_t launch_precode(int UT, const PrecodeArgs& a, cudaStream_t s, int* grid_out);
+
+// Dynamic shared memory of one CTA for the given shape (bytes).
+uint32_t detect_smem_bytes(int UT, int B, int U, int R, int exact);
+uint32_t precode_smem_bytes(int UT, int B, int U, int R);
+
+}  // namespace cgm
