@@ -89,8 +89,9 @@ def uplink(B: int, U: int, qam_bits: int, n: int, R: int, snr_db: float,
     y = np.swapaxes(y, 1, 2)
     if not noiseless:
         y = y + noise
-    return {"H": H.astype(np.complex64), "Y": y.astype(np.complex64),
-            "bits": bits, "x": x.astype(np.complex64), "N0": float(N0), "Es": float(Es),
+    return {"H": np.ascontiguousarray(H, dtype=np.complex64),
+            "Y": np.ascontiguousarray(y, dtype=np.complex64),
+            "bits": bits, "x": np.ascontiguousarray(x, dtype=np.complex64), "N0": float(N0), "Es": float(Es),
             "B": B, "U": U, "R": R, "qam_bits": qam_bits}
 
 
@@ -101,7 +102,8 @@ def downlink(B: int, U: int, qam_bits: int, n: int, R: int, snr_db: float,
     H = rayleigh(rng, n, B, U, corr)
     bits = rng.integers(0, 2, size=(n, R, U, qam_bits), dtype=np.uint8)
     T = qam_map(bits, qam_bits, Es)
-    return {"H": H.astype(np.complex64), "T": T.astype(np.complex64), "bits": bits,
+    return {"H": np.ascontiguousarray(H, dtype=np.complex64),
+            "T": np.ascontiguousarray(T, dtype=np.complex64), "bits": bits,
             "N0": float(snr_to_n0(snr_db, U, Es)), "Es": float(Es),
             "B": B, "U": U, "R": R, "qam_bits": qam_bits}
 

@@ -44,3 +44,11 @@ def test_pam_table_is_gray(q):
     order = np.argsort(lv)                      # Gray words in level order
     for a, b in zip(order[:-1], order[1:]):
         assert bin(int(a) ^ int(b)).count("1") == 1
+
+
+def test_arrays_are_contiguous():
+    for kw in ({}, {"noiseless": True}):
+        d = wl.uplink(16, 4, 4, n=3, R=2, snr_db=10.0, seed=1, **kw)
+        assert all(d[k].flags["C_CONTIGUOUS"] for k in ("H", "Y", "x"))
+    d = wl.downlink(16, 4, 4, n=3, R=2, snr_db=10.0, seed=1)
+    assert d["H"].flags["C_CONTIGUOUS"] and d["T"].flags["C_CONTIGUOUS"]
