@@ -46,7 +46,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--precision", default="fp16x3", choices=list(PRECISIONS))
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the FP32 plain path")
     return ap.parse_args()
+
+
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3, "fp16x3": 4}
 
 
 # ---------------------------------------------------------------------------
@@ -208,7 +213,8 @@ def run_ours(args):
     q = torch.empty((n, R, B), dtype=torch.complex64, device=dev)
     qn = torch.empty((n, R), dtype=torch.float32, device=dev)
     stp = torch.empty((n,), dtype=torch.int32, device=dev)
-    p = cabi.params(B, Un, QAM, K, R, N0)
+    prec = PRECISIONS[args.precision]
+    p = cabi.params(B, Un, QAM, K, R, N0, precision=prec)
     stream = torch.cuda.current_stream(dev)
 
     def step(evs=None):
@@ -255,6 +261,28 @@ def run_ours(args):
     solves_step = 2 * n * R * world
     value = solves_step / (ms_step / 1e3)
     llrs = n * R * Un * QAM * world / (ms_step / 1e3)
+
+    # the plain FP32 CUDA-core path on the same batch, for comparison
+    plain = None
+    if not args.no_plain and prec != 0:
+        pp = cabi.params(B, Un, QAM, K, R, N0, precision=0)
+        for _ in range(2):
+            cabi.cg_detect(pp, n, H, Y, xhat, mu, rho, llr, st, stream)
+            cabi.cg_precode(pp, n, H, T, q, qn, 0, stp, stream)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        reps = 5
+        e[0].record(stream)
+        for _ in range(reps):
+            cabi.cg_detect(pp, n, H, Y, xhat, mu, rho, llr, st, stream)
+        e[1].record(stream)
+        for _ in range(reps):
+            cabi.cg_precode(pp, n, H, T, q, qn, 0, stp, stream)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        pd, pq = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+        plain = {"what": "same batch, precision fp32 (CUDA-core Gram, matched filter, CG)",
+                 "value": round(2 * n * R / ((pd + pq) / 1e3), 1), "unit": "solves/s",
+                 "detect_ms": round(pd, 4), "precode_ms": round(pq, 4)}
 
     # plain per-call latency: one 1200 x 14 slot (detect + precode) per call
     lat = []
@@ -311,7 +339,7 @@ def run_ours(args):
     peaks, peak_kind = measured_peaks()
     det_bytes = detect_bytes_per_instance(B, Un, R, QAM) * n
     achieved = det_bytes / (det_ms / 1e3) / 1e9
-    traffic = profiled_traffic(f"detect_fp32_{B}x{Un}")
+    traffic = profiled_traffic(f"detect_{args.precision}_{B}x{Un}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                 "traffic": traffic, "kernel": "detect_kernel", "peak_kind": peak_kind,
@@ -335,7 +363,8 @@ def run_ours(args):
             "data": "synthetic (seeded i.i.d. CN(0,1) channels, Gray 64-QAM, AWGN at 10 dB)",
             "config": {"workload": f"uplink CG-D + downlink CG-P, B={B}, U={Un}, 64-QAM, "
                                    f"{NSC} subcarriers x {R} symbols per slot, K={K}, "
-                                   f"SNR {SNR_DB} dB, FP32",
+                                   f"SNR {SNR_DB} dB",
+                       "precision": args.precision,
                        "slots_per_step": args.slots, "instances_per_step": n,
                        "l2": "inputs larger than L2 (%.2f GB read per step)" %
                              ((det_bytes + pre_bytes) / 1e9),
@@ -350,6 +379,7 @@ def run_ours(args):
                                                            int(0.99 * len(lat)))], 4),
                            "what": "one 1200x14 slot, detect + precode, one launch each"},
             "roofline": roofline,
+            "plain_fp32": plain,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,

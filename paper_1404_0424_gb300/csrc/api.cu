@@ -83,11 +83,16 @@ int check_precode(const cg_params* p, int64_t n_inst, const void* H, const void*
   return CG_OK;
 }
 
-// Modes implemented by the FP32 kernels of this build.
+// Modes implemented by this build.
 int check_supported(const cg_params* p) {
-  if (p->precision != CG_PREC_FP32) return CG_ENOTSUP;
   if (p->amul_mode == CG_AMUL_IMPLICIT) return CG_ENOTSUP;
   return CG_OK;
+}
+
+// Tensor-core operand type (0 = BF16, 1 = FP16) and hi+lo split of a precision mode.
+void tc_mode(int precision, int* el, bool* x3) {
+  *el = (precision == CG_PREC_BF16 || precision == CG_PREC_BF16X3) ? 0 : 1;
+  *x3 = precision == CG_PREC_BF16X3 || precision == CG_PREC_FP16X3;
 }
 
 int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void* Y, void* xhat,
@@ -111,7 +116,15 @@ int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void*
   a.sigma = p->N0 / p->Es;
   a.exact = p->sinr_mode == CG_SINR_EXACT;
   a.bulk = (p->B % 2 == 0) && aligned(H, 16) && aligned(Y, 16);
-  const cudaError_t err = launch_detect(padded_users(p->U), a, s, nullptr);
+  cudaError_t err;
+  if (p->precision == CG_PREC_FP32) {
+    err = launch_detect(padded_users(p->U), a, s, nullptr);
+  } else {
+    int el;
+    bool x3;
+    tc_mode(p->precision, &el, &x3);
+    err = launch_detect_tc(padded_users(p->U), el, x3, a, s, nullptr);
+  }
   if (err == cudaErrorInvalidValue) return CG_EINVAL;
   return err == cudaSuccess ? CG_OK : CG_ECUDA;
 }
@@ -133,7 +146,15 @@ int precode_device(const cg_params* p, int64_t n_inst, const void* H, const void
   a.normalize = normalize != 0;
   a.bulk_h = ((p->B * p->U) % 2 == 0) && aligned(H, 16);
   a.bulk_t = ((p->R * p->U) % 2 == 0) && aligned(T, 16);
-  const cudaError_t err = launch_precode(padded_users(p->U), a, s, nullptr);
+  cudaError_t err;
+  if (p->precision == CG_PREC_FP32) {
+    err = launch_precode(padded_users(p->U), a, s, nullptr);
+  } else {
+    int el;
+    bool x3;
+    tc_mode(p->precision, &el, &x3);
+    err = launch_precode_tc(padded_users(p->U), el, x3, a, s, nullptr);
+  }
   if (err == cudaErrorInvalidValue) return CG_EINVAL;
   return err == cudaSuccess ? CG_OK : CG_ECUDA;
 }

@@ -23,6 +23,14 @@ int device_info(DeviceInfo* out);
 cudaError_t launch_detect(int UT, const DetectArgs& a, cudaStream_t s, int* grid_out);
 cudaError_t launch_precode(int UT, const PrecodeArgs& a, cudaStream_t s, int* grid_out);
 
+// Tensor-core variants (defined in tc.cu); el: 0 = BF16, 1 = FP16; x3: hi+lo split.
+cudaError_t launch_detect_tc(int UT, int el, bool x3, const DetectArgs& a, cudaStream_t s,
+                             int* grid_out);
+cudaError_t launch_precode_tc(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s,
+                              int* grid_out);
+uint32_t tc_detect_smem_bytes(int UT, int B, int U, int R, int exact);
+uint32_t tc_precode_smem_bytes(int UT, int B, int U, int R);
+
 // Dynamic shared memory of one CTA for the given shape (bytes).
 uint32_t detect_smem_bytes(int UT, int B, int U, int R, int exact);
 uint32_t precode_smem_bytes(int UT, int B, int U, int R);

@@ -1,0 +1,128 @@
+// Launchers of the tensor-core kernels: padded user count 8, 16 or 32,
+// FP16 or BF16 operands, one pass or hi+lo split.
+#include <mutex>
+#include <unordered_map>
+
+#include "cg_tc.cuh"
+#include "launch.cuh"
+
+namespace cgm {
+
+namespace {
+
+std::mutex g_mu;
+std::unordered_map<uint64_t, int> g_occ;
+std::unordered_map<uint64_t, int> g_attr;
+
+template <typename Kern>
+cudaError_t prepare(Kern kern, uint64_t id, int nthr, uint32_t smem, int* occ_out) {
+  DeviceInfo di;
+  if (device_info(&di) != 0) return cudaErrorUnknown;
+  if (int(smem) > di.smem_optin) return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  const uint64_t akey = (uint64_t(dev) << 48) | id;
+  const uint64_t okey = (uint64_t(dev) << 56) ^ (id << 24) ^ smem;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_attr.count(akey)) {
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, di.smem_optin);
+    if (err != cudaSuccess) return err;
+    g_attr[akey] = 1;
+  }
+  auto it = g_occ.find(okey);
+  if (it == g_occ.end()) {
+    int occ = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nthr, smem);
+    if (err != cudaSuccess) return err;
+    g_occ[okey] = occ < 1 ? 1 : occ;
+    *occ_out = g_occ[okey] * di.sm_count;
+  } else {
+    *occ_out = it->second * di.sm_count;
+  }
+  return cudaSuccess;
+}
+
+template <int UT, int EL, bool X3>
+cudaError_t det(const DetectArgs& a, cudaStream_t s, int* grid_out) {
+  constexpr int NTHR = TcCfg<UT>::NTHR;
+  const uint32_t smem = tc_detect_plan<UT>(a.B, a.U, a.R, a.exact).total;
+  int slots = 0;
+  const uint64_t id = 0x100 | (UT << 2) | (EL << 1) | (X3 ? 1 : 0);
+  cudaError_t err = prepare(detect_tc_kernel<UT, EL, X3>, id, NTHR, smem, &slots);
+  if (err != cudaSuccess) return err;
+  int64_t grid = slots < a.n_inst ? slots : a.n_inst;
+  if (grid < 1) grid = 1;
+  if (grid_out) *grid_out = int(grid);
+  detect_tc_kernel<UT, EL, X3><<<unsigned(grid), NTHR, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int UT, int EL, bool X3>
+cudaError_t pre(const PrecodeArgs& a, cudaStream_t s, int* grid_out) {
+  constexpr int NTHR = TcCfg<UT>::NTHR;
+  const uint32_t smem = tc_precode_plan<UT>(a.B, a.U, a.R).total;
+  int slots = 0;
+  const uint64_t id = 0x200 | (UT << 2) | (EL << 1) | (X3 ? 1 : 0);
+  cudaError_t err = prepare(precode_tc_kernel<UT, EL, X3>, id, NTHR, smem, &slots);
+  if (err != cudaSuccess) return err;
+  int64_t grid = slots < a.n_inst ? slots : a.n_inst;
+  if (grid < 1) grid = 1;
+  if (grid_out) *grid_out = int(grid);
+  precode_tc_kernel<UT, EL, X3><<<unsigned(grid), NTHR, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int UT>
+cudaError_t det_ut(int el, bool x3, const DetectArgs& a, cudaStream_t s, int* g) {
+  if (el == EL_BF16) return x3 ? det<UT, EL_BF16, true>(a, s, g) : det<UT, EL_BF16, false>(a, s, g);
+  return x3 ? det<UT, EL_F16, true>(a, s, g) : det<UT, EL_F16, false>(a, s, g);
+}
+
+template <int UT>
+cudaError_t pre_ut(int el, bool x3, const PrecodeArgs& a, cudaStream_t s, int* g) {
+  if (el == EL_BF16) return x3 ? pre<UT, EL_BF16, true>(a, s, g) : pre<UT, EL_BF16, false>(a, s, g);
+  return x3 ? pre<UT, EL_F16, true>(a, s, g) : pre<UT, EL_F16, false>(a, s, g);
+}
+
+}  // namespace
+
+uint32_t tc_detect_smem_bytes(int UT, int B, int U, int R, int exact) {
+  switch (UT) {
+    case 8: return tc_detect_plan<8>(B, U, R, exact).total;
+    case 16: return tc_detect_plan<16>(B, U, R, exact).total;
+    default: return tc_detect_plan<32>(B, U, R, exact).total;
+  }
+}
+
+uint32_t tc_precode_smem_bytes(int UT, int B, int U, int R) {
+  switch (UT) {
+    case 8: return tc_precode_plan<8>(B, U, R).total;
+    case 16: return tc_precode_plan<16>(B, U, R).total;
+    default: return tc_precode_plan<32>(B, U, R).total;
+  }
+}
+
+cudaError_t launch_detect_tc(int UT, int el, bool x3, const DetectArgs& a, cudaStream_t s,
+                             int* grid_out) {
+  switch (UT) {
+    case 4:
+    case 8: return det_ut<8>(el, x3, a, s, grid_out);
+    case 16: return det_ut<16>(el, x3, a, s, grid_out);
+    case 32: return det_ut<32>(el, x3, a, s, grid_out);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_precode_tc(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s,
+                              int* grid_out) {
+  switch (UT) {
+    case 4:
+    case 8: return pre_ut<8>(el, x3, a, s, grid_out);
+    case 16: return pre_ut<16>(el, x3, a, s, grid_out);
+    case 32: return pre_ut<32>(el, x3, a, s, grid_out);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace cgm
