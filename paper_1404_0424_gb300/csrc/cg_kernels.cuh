@@ -483,6 +483,94 @@ __device__ __forceinline__ void axis_llr(float x, int h, float c, float rho, flo
     if (t < h) out[t] = rho * (m0[t] - m1[t]);
 }
 
+// Compile-time form for H bits per axis: the Gray word of every level and the
+// bit partition are constants, so each level costs one FMA, one multiply and
+// H min operations.
+template <int H>
+__device__ __forceinline__ void axis_llr_t(float x, float c, float rho, float (&out)[H]) {
+  constexpr int L = 1 << H;
+  float m0[H], m1[H];
+#pragma unroll
+  for (int t = 0; t < H; ++t) m0[t] = m1[t] = INFINITY;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const float dl = fmaf(-float(2 * j - (L - 1)), c, x);
+    const float d = dl * dl;
+    const int gw = j ^ (j >> 1);
+#pragma unroll
+    for (int t = 0; t < H; ++t) {
+      if ((gw >> (H - 1 - t)) & 1)
+        m1[t] = fminf(m1[t], d);
+      else
+        m0[t] = fminf(m0[t], d);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < H; ++t) out[t] = rho * (m0[t] - m1[t]);
+}
+
+// LLRs of one user (2H bits: in-phase bits first) into dst (8-byte aligned);
+// zeros when the user has no valid mu.
+template <int H>
+__device__ __forceinline__ void store_llr(float* dst, float2 z, float c, float rho, bool valid) {
+  float v[2 * H];
+  if (valid) {
+    float lI[H], lQ[H];
+    axis_llr_t<H>(z.x, c, rho, lI);
+    axis_llr_t<H>(z.y, c, rho, lQ);
+#pragma unroll
+    for (int t = 0; t < H; ++t) {
+      v[t] = lI[t];
+      v[H + t] = lQ[t];
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < 2 * H; ++t) v[t] = 0.f;
+  }
+  float2* d2 = reinterpret_cast<float2*>(dst);
+#pragma unroll
+  for (int k = 0; k < H; ++k) d2[k] = make_float2(v[2 * k], v[2 * k + 1]);
+}
+
+// Step 5 of CG-D for instance n: x_hat, mu, rho and the max-log LLRs of
+// Eq. 4 for every (right-hand side, user), consecutive threads on
+// consecutive outputs. z = x_hat / mu; users with mu <= 0 get zero LLRs and
+// flag ST_MU_NONPOS.
+template <int UT, int NTHR>
+__device__ __forceinline__ void write_detect_outputs(const DetectArgs& a, int64_t n,
+                                                     const float2* sX, const float* sMu,
+                                                     const float* sRho, int* sStatus) {
+  const int U = a.U, R = a.R;
+  const float cq = sqrtf(3.f * a.Es / (2.f * float((1 << a.q) - 1)));
+  int flags = 0;
+  const bool full = (U == UT);
+  for (int tt = threadIdx.x; tt < R * U; tt += NTHR) {
+    const int r = full ? tt / UT : tt / U;
+    const int i = tt - r * U;
+    const float2 x = sX[r * UT + i];
+    const float mu = sMu[r * UT + i];
+    const float rho = sRho[r * UT + i];
+    const int64_t o = (n * R + r) * U + i;
+    if (a.xhat) a.xhat[o] = x;
+    if (a.mu) a.mu[o] = mu;
+    if (a.rho) a.rho[o] = rho;
+    const bool valid = mu > 0.f;
+    if (!valid) flags |= ST_MU_NONPOS;
+    if (a.llr) {
+      const float inv = valid ? 1.f / mu : 0.f;
+      const float2 z = make_float2(x.x * inv, x.y * inv);
+      float* dst = a.llr + o * a.q;
+      switch (a.q) {
+        case 2: store_llr<1>(dst, z, cq, rho, valid); break;
+        case 4: store_llr<2>(dst, z, cq, rho, valid); break;
+        case 6: store_llr<3>(dst, z, cq, rho, valid); break;
+        default: store_llr<4>(dst, z, cq, rho, valid); break;
+      }
+    }
+  }
+  if (flags) atomicOr(sStatus, flags);
+}
+
 // --------------------------------------------------------------------------
 // CG-D kernel
 // --------------------------------------------------------------------------
@@ -535,12 +623,14 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) detect_kernel(const DetectA
     int tile, slice;
     gram_tile<UT, true>(sH, sY, P.YS, a.B, U, R, P, acc, tile, slice);
     __syncthreads();  // every read of H and Y is done
+    // partial entry (slice, m, n, tile) at ((slice * TM*TN + m*TN + n) * NT + tile):
+    // consecutive threads (tiles) store to consecutive addresses
     if (tile >= 0) {
-      float2* dst = sPart + (size_t(slice) * P.NT + tile) * (TM * TN);
+      float2* dst = sPart + size_t(slice) * (TM * TN) * P.NT + tile;
 #pragma unroll
       for (int m = 0; m < TM; ++m)
 #pragma unroll
-        for (int nn = 0; nn < TN; ++nn) dst[m * TN + nn] = acc[m][nn];
+        for (int nn = 0; nn < TN; ++nn) dst[(m * TN + nn) * P.NT] = acc[m][nn];
     }
     __syncthreads();
     {
@@ -552,7 +642,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) detect_kernel(const DetectA
           s.x += t.x;
           s.y += t.y;
         }
-        const int t = e / (TM * TN), mn = e - t * (TM * TN);
+        const int mn = e / P.NT, t = e - mn * P.NT;
         const int ti = t / P.NCT, tj = t - ti * P.NCT;
         const int i = ti * TM + mn / TN, nn = mn % TN;
         const bool is_gram = tj < P.NCTH;
@@ -584,41 +674,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) detect_kernel(const DetectA
     }
 
     // ---- step 5: outputs (x_hat, mu, rho, LLRs of Eq. 4)
-    {
-      const int h = a.q / 2;
-      const float cq = sqrtf(3.f * a.Es / (2.f * float((1 << a.q) - 1)));
-      int flags = 0;
-      for (int t = tid; t < R * U; t += NTHR) {
-        const int r = t / U, i = t - (t / U) * U;
-        const float2 x = sX[r * UT + i];
-        const float mu = sMu[r * UT + i];
-        const float rho = sRho[r * UT + i];
-        const int64_t o = (n * R + r) * U + i;
-        if (a.xhat) a.xhat[o] = x;
-        if (a.mu) a.mu[o] = mu;
-        if (a.rho) a.rho[o] = rho;
-        float lI[4], lQ[4];
-        if (mu > 0.f) {
-          axis_llr(x.x / mu, h, cq, rho, lI);
-          axis_llr(x.y / mu, h, cq, rho, lQ);
-        } else {
-          flags |= ST_MU_NONPOS;
-#pragma unroll
-          for (int t2 = 0; t2 < 4; ++t2) lI[t2] = lQ[t2] = 0.f;
-        }
-        if (a.llr) {
-          float* dst = a.llr + o * a.q;
-#pragma unroll
-          for (int t2 = 0; t2 < 4; ++t2) {
-            if (t2 < h) {
-              dst[t2] = lI[t2];
-              dst[h + t2] = lQ[t2];
-            }
-          }
-        }
-      }
-      if (flags) atomicOr(sStatus, flags);
-    }
+    write_detect_outputs<UT, NTHR>(a, n, sX, sMu, sRho, sStatus);
     __syncthreads();
     if (tid == 0 && a.status) a.status[n] = *sStatus;
   }
@@ -710,11 +766,11 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) precode_kernel(const Precod
       // buffered: every slice stores its partial tile, one pass sums them in
       // slice order
       if (tile >= 0) {
-        float2* dst = sPart + (size_t(slice) * P.NT + tile) * (TM * TN);
+        float2* dst = sPart + size_t(slice) * (TM * TN) * P.NT + tile;
 #pragma unroll
         for (int m = 0; m < TM; ++m)
 #pragma unroll
-          for (int nn = 0; nn < TN; ++nn) dst[m * TN + nn] = acc[m][nn];
+          for (int nn = 0; nn < TN; ++nn) dst[(m * TN + nn) * P.NT] = acc[m][nn];
       }
       __syncthreads();
       const int E = P.NT * TM * TN;
@@ -725,7 +781,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) precode_kernel(const Precod
           s.x += t.x;
           s.y += t.y;
         }
-        const int t = e / (TM * TN), mn = e - t * (TM * TN);
+        const int mn = e / P.NT, t = e - mn * P.NT;
         const int ti = t / P.NCT, tj = t - ti * P.NCT;
         sA[(ti * TM + mn / TN) * UT + tj * TN + mn % TN] = s;
       }

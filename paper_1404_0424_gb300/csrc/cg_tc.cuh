@@ -214,6 +214,30 @@ __device__ __forceinline__ void convert_h(unsigned char* base, int B, int B8, in
   }
 }
 
+// FULL form of convert_h (U == UT, B % 8 == 0): two adjacent columns per
+// 16-byte access; the swizzle is even, so column pairs stay pairs.
+template <int EL, int NTHR, int UT>
+__device__ __forceinline__ void convert_h_full(unsigned char* base, int B) {
+  constexpr int HALF = UT / 2;
+  const float4* f = reinterpret_cast<const float4*>(base);
+  uint4* u = reinterpret_cast<uint4*>(base);
+  for (int e = threadIdx.x; e < B * HALF; e += NTHR) {
+    const int b = e / HALF, cp = e % HALF;
+    const int cp2 = cp ^ (hswz(b, UT) >> 1);
+    if (cp2 < cp) continue;
+    const float4 x1 = f[b * HALF + cp];
+    const float4 x2 = f[b * HALF + cp2];
+    const uint2 s0 = split_c<EL>(make_float2(x1.x, x1.y));
+    const uint2 s1 = split_c<EL>(make_float2(x1.z, x1.w));
+    u[b * HALF + cp2] = make_uint4(s0.x, s0.y, s1.x, s1.y);
+    if (cp2 != cp) {
+      const uint2 s2 = split_c<EL>(make_float2(x2.x, x2.y));
+      const uint2 s3 = split_c<EL>(make_float2(x2.z, x2.w));
+      u[b * HALF + cp] = make_uint4(s2.x, s2.y, s3.x, s3.y);
+    }
+  }
+}
+
 // Rows of Y (stride YS): antennas < B converted in place, B..B8-1 zeroed.
 template <int EL, int NTHR>
 __device__ __forceinline__ void convert_y(unsigned char* base, int B, int B8, int R, int YS) {
@@ -280,6 +304,140 @@ __device__ __forceinline__ void tc_gram(const uint2* __restrict__ Hc,
       }
     }
   }
+}
+
+// Same product read straight from the FP32 staging buffers (H [B][U], Y rows
+// of stride YS): each element is split into hi|lo in registers when loaded.
+// For the H columns the B fragments are the A fragment registers (column
+// n = i), so every element is loaded and converted once. FULL: U == UT and
+// B % 8 == 0, which removes every bounds predicate.
+template <int UT, int EL, bool X3, bool FULL, int NT>
+__device__ __forceinline__ void tc_gram_f32(const float2* __restrict__ sH,
+                                            const float2* __restrict__ sY, int YS, int B,
+                                            int U, int R, int wm, int wk, int WK,
+                                            float (&Cr)[NT][4], float (&Ci)[NT][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Cr[nt][k] = Ci[nt][k] = 0.f;
+  const int Uc = FULL ? UT : U;
+  const int KS = FULL ? B / 8 : (B + 7) / 8;
+  const int ks0 = (wk * KS) / WK, ks1 = ((wk + 1) * KS) / WK;
+  const int i0 = wm * 16 + g, i1 = i0 + 8;
+  const bool r0ok = FULL ? (wm * 16 < UT) : (i0 < U);
+  const bool r1ok = FULL ? (wm * 16 + 8 < UT) : (i1 < U);
+  const int NTH = UT / 8;  // n-tiles that hold H columns when FULL
+  const int nta = (Uc + R + 7) / 8;
+  const float2 z2 = make_float2(0.f, 0.f);
+  for (int ks = ks0; ks < ks1; ++ks) {
+    const int b0 = ks * 8 + t, b1 = b0 + 4;
+    const bool v0 = FULL || b0 < B, v1 = FULL || b1 < B;
+    const uint2 x0 = split_c<EL>((r0ok && v0) ? sH[b0 * Uc + i0] : z2);
+    const uint2 x1 = split_c<EL>((r1ok && v0) ? sH[b0 * Uc + i1] : z2);
+    const uint2 x2 = split_c<EL>((r0ok && v1) ? sH[b1 * Uc + i0] : z2);
+    const uint2 x3 = split_c<EL>((r1ok && v1) ? sH[b1 * Uc + i1] : z2);
+    const uint32_t ah[4] = {x0.x, x1.x, x2.x, x3.x};
+    const uint32_t al[4] = {x0.y, x1.y, x2.y, x3.y};
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      if (nt >= nta) continue;
+      uint2 z0, z1;
+      if (FULL && nt < NTH && nt * 8 == wm * 16) {
+        z0 = x0;
+        z1 = x2;
+      } else if (FULL && nt < NTH && nt * 8 == wm * 16 + 8) {
+        z0 = x1;
+        z1 = x3;
+      } else {
+        const int n = nt * 8 + g;
+        float2 f0 = z2, f1 = z2;
+        if (FULL ? (nt < NTH) : (n < U)) {
+          if (v0) f0 = sH[b0 * Uc + n];
+          if (v1) f1 = sH[b1 * Uc + n];
+        } else if (n - Uc < R) {
+          if (v0) f0 = sY[(n - Uc) * YS + b0];
+          if (v1) f1 = sY[(n - Uc) * YS + b1];
+        }
+        z0 = split_c<EL>(f0);
+        z1 = split_c<EL>(f1);
+      }
+      // real part: [Hr Hi] . [Zr Zi]; imaginary part: [Hr Hi] . [Zi -Zr]
+      mma_split<EL, X3>(Cr[nt], ah, al, z0.x, z1.x, z0.y, z1.y);
+      mma_split<EL, X3>(Ci[nt], ah, al, swap_neg(z0.x), swap_neg(z1.x), swap_neg(z0.y),
+                        swap_neg(z1.y));
+    }
+  }
+}
+
+// Warp w sums n-tile w (w + NWARP, ...) over the WK partials of each m-tile,
+// in order, and stores it: Gram entries as the upper triangle of A = G +
+// sigma I mirrored (exactly Hermitian) with its hi|lo split, diag(G), and
+// matched filters. Padded users are zeroed by the caller's layout init.
+template <int UT, int EL, int NT>
+__device__ __forceinline__ void tc_reduce_warp(const float* __restrict__ part, int WK, int U,
+                                               int R, float sigma, float2* sA, uint2* sAc,
+                                               float2* sBm, float* sGd) {
+  constexpr int WM = TcCfg<UT>::WM, SP = TcCfg<UT>::SP, NWARP = TcCfg<UT>::NWARP;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int nta = (U + R + 7) / 8;
+  for (int job = warp; job < WM * nta; job += NWARP) {
+    const int wm = job / nta, nt = job - wm * nta;
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int wk = 0; wk < WK; ++wk) {
+      const int w = wk * WM + wm;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        re[d] += part[((w * NT + nt) * 8 + d) * 32 + lane];
+        im[d] += part[((w * NT + nt) * 8 + 4 + d) * 32 + lane];
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int i = wm * 16 + g + ((d & 2) ? 8 : 0);
+      const int n = nt * 8 + 2 * t + (d & 1);
+      if (i >= U || n >= U + R) continue;
+      const float2 s = make_float2(re[d], im[d]);
+      if (n < U) {
+        if (i < n) {
+          const float2 c = make_float2(s.x, -s.y);
+          sA[i * UT + n] = s;
+          sA[n * UT + i] = c;
+          sAc[i * SP + n] = split_c<EL>(s);
+          sAc[n * SP + i] = split_c<EL>(c);
+        } else if (i == n) {
+          const float2 a = make_float2(s.x + sigma, 0.f);
+          sA[i * UT + i] = a;
+          sAc[i * SP + i] = split_c<EL>(a);
+          sGd[i] = s.x;
+        }
+      } else {
+        sBm[(n - U) * UT + i] = s;
+      }
+    }
+  }
+}
+
+// Zero entries of padded users (i or j >= U) in A, its split, diag(G) and
+// the matched filters; disjoint from what tc_reduce_warp writes.
+template <int UT>
+__device__ __forceinline__ void tc_zero_padding(int U, int R, float2* sA, uint2* sAc,
+                                                float2* sBm, float* sGd, int nthr) {
+  constexpr int SP = TcCfg<UT>::SP;
+  if (U == UT) return;
+  for (int e = threadIdx.x; e < UT * UT; e += nthr) {
+    const int i = e / UT, j = e - (e / UT) * UT;
+    if (i >= U || j >= U) {
+      sA[e] = make_float2(0.f, 0.f);
+      sAc[i * SP + j] = make_uint2(0u, 0u);
+      if (i == j) sGd[i] = 0.f;
+    }
+  }
+  if (sBm != nullptr)
+    for (int e = threadIdx.x; e < R * UT; e += nthr) {
+      const int r = e / UT, i = e - (e / UT) * UT;
+      if (i >= U) sBm[r * UT + i] = make_float2(0.f, 0.f);
+    }
 }
 
 // Reduces the warps' partial tiles (same wm, wk = 0..WK-1, in order) and
@@ -550,14 +708,15 @@ struct TcCg {
 // CG-D, tensor-core variant
 // ---------------------------------------------------------------------------
 
-template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(TcCfg<UT>::NTHR) detect_tc_kernel(const DetectArgs a) {
+template <int UT, int EL, bool X3, bool FULL>
+__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
+    detect_tc_kernel(const DetectArgs a) {
   using C = TcCfg<UT>;
   constexpr int NTHR = C::NTHR, WM = C::WM, WK = C::WK, NT = C::NTD, SP = C::SP;
   extern __shared__ __align__(128) unsigned char smem[];
   const TcPlan P = tc_detect_plan<UT>(a.B, a.U, a.R, a.exact);
-  const uint2* Hc = reinterpret_cast<const uint2*>(smem + P.H);
-  const uint2* Yc = reinterpret_cast<const uint2*>(smem + P.Y);
+  const float2* sHf = reinterpret_cast<const float2*>(smem + P.H);
+  const float2* sYf = reinterpret_cast<const float2*>(smem + P.Y);
   float* part = reinterpret_cast<float*>(smem + P.Part);
   float2* sA = reinterpret_cast<float2*>(smem + P.A);
   uint2* sAc = reinterpret_cast<uint2*>(smem + P.Ac);
@@ -609,12 +768,10 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR) detect_tc_kernel(const Detect
     }
     if (tid == 0) *sStatus = 0;
 
-    // ---- step 2: hi|lo operands, then G and H^H Y on the tensor cores
-    convert_h<EL, NTHR>(smem + P.H, B, P.B8, U);
-    convert_y<EL, NTHR>(smem + P.Y, B, P.B8, R, P.YS);
-    __syncthreads();
+    // ---- step 2: G and H^H Y on the tensor cores (Algorithm 1 line 5)
     float Cr[NT][4], Ci[NT][4];
-    tc_gram<UT, EL, X3, NT>(Hc, Yc, P.YS, P.B8, U, Nz, warp % WM, warp / WM, WK, Cr, Ci);
+    tc_gram_f32<UT, EL, X3, FULL, NT>(sHf, sYf, P.YS, B, U, R, warp % WM, warp / WM, WK, Cr,
+                                      Ci);
     __syncthreads();  // the H/Y region becomes the partial buffer
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt)
@@ -624,7 +781,8 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR) detect_tc_kernel(const Detect
         part[((warp * NT + nt) * 8 + 4 + d) * 32 + lane] = Ci[nt][d];
       }
     __syncthreads();
-    tc_reduce<UT, EL, NT>(part, WK, U, R, Nz, a.sigma, sA, sAc, sBm, sGd, NTHR);
+    tc_reduce_warp<UT, EL, NT>(part, WK, U, R, a.sigma, sA, sAc, sBm, sGd);
+    tc_zero_padding<UT>(U, R, sA, sAc, sBm, sGd, NTHR);
     __syncthreads();
     const int64_t next = n + gridDim.x;
     if (a.bulk && !a.exact && next < a.n_inst && tid == 0) {
@@ -681,41 +839,7 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR) detect_tc_kernel(const Detect
     }
 
     // ---- step 5: outputs (x_hat, mu, rho, LLRs of Eq. 4)
-    {
-      const int h = a.q / 2;
-      const float cq = sqrtf(3.f * a.Es / (2.f * float((1 << a.q) - 1)));
-      int flags = 0;
-      for (int tt = tid; tt < R * U; tt += NTHR) {
-        const int r = tt / U, i = tt - (tt / U) * U;
-        const float2 x = sX[r * UT + i];
-        const float mu = sMu[r * UT + i];
-        const float rho = sRho[r * UT + i];
-        const int64_t o = (n * R + r) * U + i;
-        if (a.xhat) a.xhat[o] = x;
-        if (a.mu) a.mu[o] = mu;
-        if (a.rho) a.rho[o] = rho;
-        float lI[4], lQ[4];
-        if (mu > 0.f) {
-          axis_llr(x.x / mu, h, cq, rho, lI);
-          axis_llr(x.y / mu, h, cq, rho, lQ);
-        } else {
-          flags |= ST_MU_NONPOS;
-#pragma unroll
-          for (int t2 = 0; t2 < 4; ++t2) lI[t2] = lQ[t2] = 0.f;
-        }
-        if (a.llr) {
-          float* dst = a.llr + o * a.q;
-#pragma unroll
-          for (int t2 = 0; t2 < 4; ++t2) {
-            if (t2 < h) {
-              dst[t2] = lI[t2];
-              dst[h + t2] = lQ[t2];
-            }
-          }
-        }
-      }
-      if (flags) atomicOr(sStatus, flags);
-    }
+    write_detect_outputs<UT, NTHR>(a, n, sX, sMu, sRho, sStatus);
     __syncthreads();
     if (tid == 0 && a.status) a.status[n] = *sStatus;
     (void)SP;
@@ -726,8 +850,9 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR) detect_tc_kernel(const Detect
 // CG-P, tensor-core variant
 // ---------------------------------------------------------------------------
 
-template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(TcCfg<UT>::NTHR) precode_tc_kernel(const PrecodeArgs a) {
+template <int UT, int EL, bool X3, bool FULL>
+__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
+    precode_tc_kernel(const PrecodeArgs a) {
   using C = TcCfg<UT>;
   constexpr int NTHR = C::NTHR, NWARP = C::NWARP, WM = C::WM, WK = C::WK, NT = C::NTP;
   constexpr int SP = C::SP, KSV = C::KSC;
@@ -783,7 +908,10 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR) precode_tc_kernel(const Preco
     if (tid == 0) *sStatus = 0;
 
     // ---- step 2: A = H^H H + sigma I on the tensor cores (Algorithm 1 line 6)
-    convert_h<EL, NTHR>(smem + P.H, B, P.B8, U);
+    if (FULL)
+      convert_h_full<EL, NTHR, UT>(smem + P.H, B);
+    else
+      convert_h<EL, NTHR>(smem + P.H, B, P.B8, U);
     __syncthreads();
     {
       float Cr[NT][4], Ci[NT][4];

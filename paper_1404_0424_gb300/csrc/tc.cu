@@ -43,46 +43,61 @@ cudaError_t prepare(Kern kern, uint64_t id, int nthr, uint32_t smem, int* occ_ou
   return cudaSuccess;
 }
 
-template <int UT, int EL, bool X3>
+template <int UT, int EL, bool X3, bool FULL>
 cudaError_t det(const DetectArgs& a, cudaStream_t s, int* grid_out) {
   constexpr int NTHR = TcCfg<UT>::NTHR;
   const uint32_t smem = tc_detect_plan<UT>(a.B, a.U, a.R, a.exact).total;
   int slots = 0;
-  const uint64_t id = 0x100 | (UT << 2) | (EL << 1) | (X3 ? 1 : 0);
-  cudaError_t err = prepare(detect_tc_kernel<UT, EL, X3>, id, NTHR, smem, &slots);
+  const uint64_t id = 0x1000 | (UT << 3) | (EL << 2) | (X3 ? 2 : 0) | (FULL ? 1 : 0);
+  cudaError_t err = prepare(detect_tc_kernel<UT, EL, X3, FULL>, id, NTHR, smem, &slots);
   if (err != cudaSuccess) return err;
   int64_t grid = slots < a.n_inst ? slots : a.n_inst;
   if (grid < 1) grid = 1;
   if (grid_out) *grid_out = int(grid);
-  detect_tc_kernel<UT, EL, X3><<<unsigned(grid), NTHR, smem, s>>>(a);
+  detect_tc_kernel<UT, EL, X3, FULL><<<unsigned(grid), NTHR, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int UT, int EL, bool X3>
+template <int UT, int EL, bool X3, bool FULL>
 cudaError_t pre(const PrecodeArgs& a, cudaStream_t s, int* grid_out) {
   constexpr int NTHR = TcCfg<UT>::NTHR;
   const uint32_t smem = tc_precode_plan<UT>(a.B, a.U, a.R).total;
   int slots = 0;
-  const uint64_t id = 0x200 | (UT << 2) | (EL << 1) | (X3 ? 1 : 0);
-  cudaError_t err = prepare(precode_tc_kernel<UT, EL, X3>, id, NTHR, smem, &slots);
+  const uint64_t id = 0x2000 | (UT << 3) | (EL << 2) | (X3 ? 2 : 0) | (FULL ? 1 : 0);
+  cudaError_t err = prepare(precode_tc_kernel<UT, EL, X3, FULL>, id, NTHR, smem, &slots);
   if (err != cudaSuccess) return err;
   int64_t grid = slots < a.n_inst ? slots : a.n_inst;
   if (grid < 1) grid = 1;
   if (grid_out) *grid_out = int(grid);
-  precode_tc_kernel<UT, EL, X3><<<unsigned(grid), NTHR, smem, s>>>(a);
+  precode_tc_kernel<UT, EL, X3, FULL><<<unsigned(grid), NTHR, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// FULL instantiations: U equals the padded user count and B is a multiple of 8.
+template <int UT, int EL, bool X3>
+cudaError_t det_f(const DetectArgs& a, cudaStream_t s, int* g) {
+  const bool full = a.U == UT && a.B % 8 == 0;
+  return full ? det<UT, EL, X3, true>(a, s, g) : det<UT, EL, X3, false>(a, s, g);
+}
+
+template <int UT, int EL, bool X3>
+cudaError_t pre_f(const PrecodeArgs& a, cudaStream_t s, int* g) {
+  const bool full = a.U == UT && a.B % 8 == 0;
+  return full ? pre<UT, EL, X3, true>(a, s, g) : pre<UT, EL, X3, false>(a, s, g);
 }
 
 template <int UT>
 cudaError_t det_ut(int el, bool x3, const DetectArgs& a, cudaStream_t s, int* g) {
-  if (el == EL_BF16) return x3 ? det<UT, EL_BF16, true>(a, s, g) : det<UT, EL_BF16, false>(a, s, g);
-  return x3 ? det<UT, EL_F16, true>(a, s, g) : det<UT, EL_F16, false>(a, s, g);
+  if (el == EL_BF16)
+    return x3 ? det_f<UT, EL_BF16, true>(a, s, g) : det_f<UT, EL_BF16, false>(a, s, g);
+  return x3 ? det_f<UT, EL_F16, true>(a, s, g) : det_f<UT, EL_F16, false>(a, s, g);
 }
 
 template <int UT>
 cudaError_t pre_ut(int el, bool x3, const PrecodeArgs& a, cudaStream_t s, int* g) {
-  if (el == EL_BF16) return x3 ? pre<UT, EL_BF16, true>(a, s, g) : pre<UT, EL_BF16, false>(a, s, g);
-  return x3 ? pre<UT, EL_F16, true>(a, s, g) : pre<UT, EL_F16, false>(a, s, g);
+  if (el == EL_BF16)
+    return x3 ? pre_f<UT, EL_BF16, true>(a, s, g) : pre_f<UT, EL_BF16, false>(a, s, g);
+  return x3 ? pre_f<UT, EL_F16, true>(a, s, g) : pre_f<UT, EL_F16, false>(a, s, g);
 }
 
 }  // namespace
