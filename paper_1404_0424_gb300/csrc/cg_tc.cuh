@@ -506,7 +506,9 @@ __device__ __forceinline__ void tc_reduce(const float* __restrict__ part, int WK
 // i = 16 mt + g + 8h (h = 0, 1): the positions of the m16n8 accumulator.
 // Lanes with the same t hold one right-hand side; inner products reduce over
 // the eight lanes g = 0..7 (butterflies on lane bits 2-4). p travels through
-// sP (row r, stride SP) into the B-fragment layout before each product.
+// sP (row r, stride SP) into the B-fragment layout before each product. The
+// A fragments (hi|lo of A) stay in registers for all iterations; the three
+// split products accumulate separately so no mma waits on more than KS others.
 template <int UT, int EL>
 struct TcCg {
   static constexpr int MT = TcCfg<UT>::WM, KS = TcCfg<UT>::KSC, SP = TcCfg<UT>::SP;
@@ -515,25 +517,55 @@ struct TcCg {
   float rrn[2], a1[2], a2[2], be1[2], be2[2];
   bool active[2], broke[2];
   int kd[2];
+  uint32_t fah[MT][KS][4], fal[MT][KS][4];  // A fragments, hi and lo
 
-  __device__ __forceinline__ static float reduce8(float x) {
-    float s = x, c = 0.f;
+  // Compensated butterfly over the eight lanes that share t, for two
+  // independent sums at once (TwoSum error terms carried alongside).
+  __device__ __forceinline__ static void reduce8x2(float& x0, float& x1) {
+    float s0 = x0, s1 = x1, c0 = 0.f, c1 = 0.f;
 #pragma unroll
     for (int off = 4; off < 32; off <<= 1) {
-      const float so = __shfl_xor_sync(0xffffffffu, s, off);
-      const float co = __shfl_xor_sync(0xffffffffu, c, off);
-      const float tt = s + so;
-      const float bp = tt - s;
-      const float err = (s - (tt - bp)) + (so - bp);
-      s = tt;
-      c = (c + co) + err;
+      const float so0 = __shfl_xor_sync(0xffffffffu, s0, off);
+      const float so1 = __shfl_xor_sync(0xffffffffu, s1, off);
+      const float co0 = __shfl_xor_sync(0xffffffffu, c0, off);
+      const float co1 = __shfl_xor_sync(0xffffffffu, c1, off);
+      const float t0 = s0 + so0, t1 = s1 + so1;
+      const float b0 = t0 - s0, b1 = t1 - s1;
+      const float e0 = (s0 - (t0 - b0)) + (so0 - b0);
+      const float e1 = (s1 - (t1 - b1)) + (so1 - b1);
+      s0 = t0;
+      s1 = t1;
+      c0 = (c0 + co0) + e0;
+      c1 = (c1 + co1) + e1;
     }
-    return s + c;
+    x0 = s0 + c0;
+    x1 = s1 + c1;
+  }
+
+  __device__ __forceinline__ void load_a(const uint2* __restrict__ sAc) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint2 z = make_uint2(0u, 0u);
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const int i0 = mt * 16 + g, i1 = i0 + 8;
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const int j0 = ks * 8 + t, j1 = j0 + 4;
+        const uint2 x0 = (i0 < UT && j0 < UT) ? sAc[i0 * SP + j0] : z;
+        const uint2 x1 = (i1 < UT && j0 < UT) ? sAc[i1 * SP + j0] : z;
+        const uint2 x2 = (i0 < UT && j1 < UT) ? sAc[i0 * SP + j1] : z;
+        const uint2 x3 = (i1 < UT && j1 < UT) ? sAc[i1 * SP + j1] : z;
+        fah[mt][ks][0] = x0.x; fal[mt][ks][0] = x0.y;
+        fah[mt][ks][1] = x1.x; fal[mt][ks][1] = x1.y;
+        fah[mt][ks][2] = x2.x; fal[mt][ks][2] = x2.y;
+        fah[mt][ks][3] = x3.x; fal[mt][ks][3] = x3.y;
+      }
+    }
   }
 
   // e = A p for the warp's eight right-hand sides; E[mt][d] in accumulator layout.
-  __device__ __forceinline__ void matvec(const uint2* __restrict__ sAc, float2* sP, int n0,
-                                         int U, float (&Er)[MT][4], float (&Ei)[MT][4]) {
+  __device__ __forceinline__ void matvec(float2* sP, int n0, float (&Er)[MT][4],
+                                         float (&Ei)[MT][4]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
@@ -546,7 +578,7 @@ struct TcCg {
         }
       }
     __syncwarp();
-    uint32_t bh[KS][2][2], bl[KS][2][2];  // [ks][reg][B1/B2]
+    uint32_t bh[KS][2][2], bl[KS][2][2];  // [ks][reg][real / imaginary part]
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
 #pragma unroll
@@ -563,36 +595,35 @@ struct TcCg {
     __syncwarp();
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt) {
+      float hh[2][4], hl[2][4], lh[2][4];  // [re/im][d]
 #pragma unroll
-      for (int k = 0; k < 4; ++k) Er[mt][k] = Ei[mt][k] = 0.f;
-      const int i0 = mt * 16 + g, i1 = i0 + 8;
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) hh[c][k] = hl[c][k] = lh[c][k] = 0.f;
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks) {
-        const int j0 = ks * 8 + t, j1 = j0 + 4;
-        uint32_t ah[4], al[4];
-        const uint2 z = make_uint2(0u, 0u);
-        const uint2 x0 = (i0 < UT && j0 < UT) ? sAc[i0 * SP + j0] : z;
-        const uint2 x1 = (i1 < UT && j0 < UT) ? sAc[i1 * SP + j0] : z;
-        const uint2 x2 = (i0 < UT && j1 < UT) ? sAc[i0 * SP + j1] : z;
-        const uint2 x3 = (i1 < UT && j1 < UT) ? sAc[i1 * SP + j1] : z;
-        ah[0] = x0.x; al[0] = x0.y;
-        ah[1] = x1.x; al[1] = x1.y;
-        ah[2] = x2.x; al[2] = x2.y;
-        ah[3] = x3.x; al[3] = x3.y;
-        mma_split<EL, true>(Er[mt], ah, al, bh[ks][0][0], bh[ks][1][0], bl[ks][0][0],
-                            bl[ks][1][0]);
-        mma_split<EL, true>(Ei[mt], ah, al, bh[ks][0][1], bh[ks][1][1], bl[ks][0][1],
-                            bl[ks][1][1]);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          mma16816<EL>(hh[c], fah[mt][ks], bh[ks][0][c], bh[ks][1][c]);
+          mma16816<EL>(hl[c], fah[mt][ks], bl[ks][0][c], bl[ks][1][c]);
+          mma16816<EL>(lh[c], fal[mt][ks], bh[ks][0][c], bh[ks][1][c]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Er[mt][k] = hh[0][k] + (hl[0][k] + lh[0][k]);
+        Ei[mt][k] = hh[1][k] + (hl[1][k] + lh[1][k]);
       }
     }
-    (void)U;
   }
 
   // Lines 7-16 of Algorithm 1 with the approximate tracker of Eqs. 11-13.
-  // b[mt][h][rr] is the right-hand side of the owned positions (0 if padded).
+  // res[mt][h][rr] holds the right-hand side of the owned positions on entry
+  // (0 where padded). Quotients use the fast reciprocal (<= 2 ulp).
   __device__ __forceinline__ void run(const uint2* __restrict__ sAc, const float2* __restrict__ sA,
                                       float2* sP, int n0, int U, int R, int K, float* sAB) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    load_a(sAc);
     float D[MT][2];
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
@@ -601,20 +632,27 @@ struct TcCg {
         const int i = mt * 16 + g + 8 * h;
         D[mt][h] = (i < U) ? sA[i * UT + i].x : 0.f;
       }
+    float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-      float s = 0.f;
+    for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-      for (int mt = 0; mt < MT; ++mt)
+      for (int h = 0; h < 2; ++h) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int rr = 0; rr < 2; ++rr) {
           v[mt][h][rr] = make_float2(0.f, 0.f);
           p[mt][h][rr] = res[mt][h][rr];
           l1[mt][h][rr] = l2[mt][h][rr] = l3[mt][h][rr] = 0.f;
-          s = fmaf(res[mt][h][rr].x, res[mt][h][rr].x, fmaf(res[mt][h][rr].y, res[mt][h][rr].y, s));
         }
-      rrn[rr] = reduce8(s);
-      a1[rr] = a2[rr] = 1.f;
+        s0 = fmaf(res[mt][h][0].x, res[mt][h][0].x, fmaf(res[mt][h][0].y, res[mt][h][0].y, s0));
+        s1 = fmaf(res[mt][h][1].x, res[mt][h][1].x, fmaf(res[mt][h][1].y, res[mt][h][1].y, s1));
+      }
+    reduce8x2(s0, s1);
+    rrn[0] = s0;
+    rrn[1] = s1;
+    float ia1[2], ia2[2];  // 1 / alpha_{k-1}, 1 / alpha_{k-2}
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      a1[rr] = a2[rr] = ia1[rr] = ia2[rr] = 1.f;
       be1[rr] = be2[rr] = 0.f;
       active[rr] = (n0 + 2 * t + rr) < R;
       broke[rr] = false;
@@ -629,29 +667,26 @@ struct TcCg {
         }
       if (!__any_sync(0xffffffffu, active[0] || active[1])) break;
       float Er[MT][4], Ei[MT][4];
-      matvec(sAc, sP, n0, U, Er, Ei);
-      float pe[2];
+      matvec(sP, n0, Er, Ei);
+      float pe[2] = {0.f, 0.f};
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        float s = 0.f;
+      for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const float2 pp = p[mt][h][rr];
-            s = fmaf(pp.x, Er[mt][2 * h + rr], fmaf(pp.y, Ei[mt][2 * h + rr], s));
+            pe[rr] = fmaf(pp.x, Er[mt][2 * h + rr], fmaf(pp.y, Ei[mt][2 * h + rr], pe[rr]));
           }
-        pe[rr] = reduce8(s);
-      }
-      float rrnew[2], alpha[2];
+      reduce8x2(pe[0], pe[1]);
+      float alpha[2], rrnew[2] = {0.f, 0.f};
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
         if (active[rr] && !(pe[rr] > 0.f)) {
           active[rr] = false;
           broke[rr] = true;
         }
-        alpha[rr] = active[rr] ? rrn[rr] / pe[rr] : 0.f;
-        float s = 0.f;
+        alpha[rr] = active[rr] ? __fdividef(rrn[rr], pe[rr]) : 0.f;
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
@@ -662,16 +697,18 @@ struct TcCg {
               res[mt][h][rr].x = fmaf(-alpha[rr], Er[mt][2 * h + rr], res[mt][h][rr].x);
               res[mt][h][rr].y = fmaf(-alpha[rr], Ei[mt][2 * h + rr], res[mt][h][rr].y);
             }
-            s = fmaf(res[mt][h][rr].x, res[mt][h][rr].x,
-                     fmaf(res[mt][h][rr].y, res[mt][h][rr].y, s));
+            rrnew[rr] = fmaf(res[mt][h][rr].x, res[mt][h][rr].x,
+                             fmaf(res[mt][h][rr].y, res[mt][h][rr].y, rrnew[rr]));
           }
-        rrnew[rr] = reduce8(s);
       }
+      reduce8x2(rrnew[0], rrnew[1]);
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
         if (!active[rr]) continue;
         const float al = alpha[rr];
-        const float beta = rrnew[rr] / rrn[rr];
+        const float beta = __fdividef(rrnew[rr], rrn[rr]);
+        const float c1 = al * (1.f + be1[rr]) * ia1[rr];
+        const float c2 = al * be2[rr] * ia2[rr];
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
@@ -680,10 +717,8 @@ struct TcCg {
             p[mt][h][rr].y = fmaf(beta, p[mt][h][rr].y, res[mt][h][rr].y);
             const float lk = (k == 1) ? al
                                       : l1[mt][h][rr] +
-                                            (al * (1.f + be1[rr]) / a1[rr] - al * D[mt][h]) *
-                                                (l1[mt][h][rr] - l2[mt][h][rr]) -
-                                            (al * be2[rr] / a2[rr]) *
-                                                (l2[mt][h][rr] - l3[mt][h][rr]);
+                                            (c1 - al * D[mt][h]) * (l1[mt][h][rr] - l2[mt][h][rr]) -
+                                            c2 * (l2[mt][h][rr] - l3[mt][h][rr]);
             l3[mt][h][rr] = l2[mt][h][rr];
             l2[mt][h][rr] = l1[mt][h][rr];
             l1[mt][h][rr] = lk;
@@ -695,6 +730,8 @@ struct TcCg {
         }
         a2[rr] = a1[rr];
         a1[rr] = al;
+        ia2[rr] = ia1[rr];
+        ia1[rr] = __fdividef(1.f, al);
         be2[rr] = be1[rr];
         be1[rr] = beta;
         rrn[rr] = rrnew[rr];
@@ -950,10 +987,10 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
 #pragma unroll
           for (int rr = 0; rr < 2; ++rr) cg.p[mt][h][rr] = cg.v[mt][h][rr];
       float Er[WM][4], Ei[WM][4];
-      cg.matvec(sAc, sP, n0, U, Er, Ei);
+      cg.matvec(sP, n0, Er, Ei);
+      float qq2[2] = {0.f, 0.f};
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        float s = 0.f;
+      for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
         for (int mt = 0; mt < WM; ++mt)
 #pragma unroll
@@ -961,9 +998,12 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
             const float2 vv = cg.v[mt][h][rr];
             const float wx = fmaf(-a.sigma, vv.x, Er[mt][2 * h + rr]);
             const float wy = fmaf(-a.sigma, vv.y, Ei[mt][2 * h + rr]);
-            s = fmaf(vv.x, wx, fmaf(vv.y, wy, s));
+            qq2[rr] = fmaf(vv.x, wx, fmaf(vv.y, wy, qq2[rr]));
           }
-        const float qq = TcCg<UT, EL>::reduce8(s);
+      TcCg<UT, EL>::reduce8x2(qq2[0], qq2[1]);
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const float qq = qq2[rr];
         const int r = n0 + 2 * t + rr;
         if (g == 0 && r < R) {
           const float nr = sqrtf(fmaxf(qq, 0.f));
