@@ -133,6 +133,62 @@ int cg_precode_host(const cg_params* p, int64_t n_inst, const void* H, const voi
                     void* q, float* qnorm, int32_t normalize, int32_t* status,
                     void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched uneven problems (one plan, one CUDA-graph launch per run)
+ * ------------------------------------------------------------------------ */
+
+#define CG_OP_DETECT 0
+#define CG_OP_PRECODE 1
+
+/* One problem of a batch: n_inst instances of one shape, with its own
+ * parameters and its own DEVICE buffers in the layouts above.
+ *   op = CG_OP_DETECT:  in = Y, out = xhat, mu, rho, aux = llr  (NULL = not written)
+ *   op = CG_OP_PRECODE: in = T, out = q (required), aux = qnorm; mu, rho unused;
+ *                       normalize selects s = q / ||q||.
+ * B, U, R, K, qam_bits, N0, Es and sinr_mode follow cg_params. */
+typedef struct cg_desc {
+  int32_t op, B, U, R, K, qam_bits, sinr_mode, normalize;
+  float N0, Es;
+  int64_t n_inst;
+  const void* H;
+  const void* in;
+  void* out;
+  float* mu;
+  float* rho;
+  float* aux;
+  int32_t* status;
+} cg_desc;
+
+/* Precision value for plans: let the autotuner pick among the modes that
+ * meet FP32-level accuracy (CG_PREC_FP32, CG_PREC_FP16X3, CG_PREC_BF16X3). */
+#define CG_PREC_AUTO (-1)
+
+typedef struct cg_plan cg_plan;
+
+/* Builds a plan for n problems (descs is a HOST array; the library keeps a
+ * device copy, so the descriptor memory may be reused after the call).
+ * Problems are grouped into bins by operation and padded user count; each
+ * bin runs one persistent fused kernel whose CTAs claim (problem, instance)
+ * work units from a device counter, so uneven problems balance across SMs.
+ * All bins are captured once into a CUDA graph on `stream` and replayed by
+ * cg_plan_run. precision is a CG_PREC_* value or CG_PREC_AUTO, which times
+ * the candidates on the batch itself (the plan's first run is then done;
+ * results are cached per device and shape class). The plan owns its device
+ * memory until cg_plan_destroy. The buffers named by the descriptors must
+ * stay valid while the plan is used. Returns CG_EINVAL for an invalid
+ * descriptor (the first bad index is reported in *bad_index if non-NULL). */
+int cg_plan_create(const cg_desc* descs, int64_t n, int32_t precision, void* stream,
+                   cg_plan** plan, int64_t* bad_index);
+
+/* Enqueues one run of the plan on `stream` (a single graph launch). */
+int cg_plan_run(cg_plan* plan, void* stream);
+
+/* Precision chosen for the plan (after autotuning) and the number of bins. */
+int cg_plan_info(const cg_plan* plan, int32_t* precision, int32_t* n_bins);
+
+/* Releases the plan (waits for its outstanding runs first). */
+int cg_plan_destroy(cg_plan* plan);
+
 /* Frees the workspace of the *_host calls on the current device. */
 int cg_release_workspace(void);
 

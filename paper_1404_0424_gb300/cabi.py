@@ -39,6 +39,16 @@ class CgParams(ctypes.Structure):
                 ("amul_mode", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
+class CgDesc(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("B", ctypes.c_int32), ("U", ctypes.c_int32),
+                ("R", ctypes.c_int32), ("K", ctypes.c_int32), ("qam_bits", ctypes.c_int32),
+                ("sinr_mode", ctypes.c_int32), ("normalize", ctypes.c_int32),
+                ("N0", ctypes.c_float), ("Es", ctypes.c_float), ("n_inst", ctypes.c_int64),
+                ("H", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("mu", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("aux", ctypes.c_void_p),
+                ("status", ctypes.c_void_p)]
+
+
 class CgError(RuntimeError):
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {cg_strerror(code)} ({code})")
@@ -60,6 +70,11 @@ _SIGS = {
     "cg_precode_host": [ctypes.POINTER(CgParams), ctypes.c_int64, _VP, _VP, _VP, _VP,
                         ctypes.c_int32, _VP, _VP],
     "cg_release_workspace": [],
+    "cg_plan_create": [ctypes.POINTER(CgDesc), ctypes.c_int64, ctypes.c_int32, _VP,
+                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)],
+    "cg_plan_run": [_VP, _VP],
+    "cg_plan_info": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+    "cg_plan_destroy": [_VP],
     "cg_strerror": [ctypes.c_int],
     "cg_version": [],
 }
@@ -147,6 +162,40 @@ def cg_precode_host(p: CgParams, n_inst, H, T, q, qnorm=None, normalize=0, statu
                     stream=None) -> int:
     return library().cg_precode_host(ctypes.byref(p), int(n_inst), _ptr(H), _ptr(T), _ptr(q),
                                      _ptr(qnorm), int(normalize), _ptr(status), _stream(stream))
+
+
+def cg_plan_create(descs, precision=-1, stream=None):
+    """descs: sequence of CgDesc. Returns (rc, plan handle or None, bad_index)."""
+    arr = (CgDesc * max(len(descs), 1))(*descs)
+    plan = ctypes.c_void_p()
+    bad = ctypes.c_int64(-1)
+    rc = library().cg_plan_create(arr, len(descs), int(precision), _stream(stream),
+                                  ctypes.byref(plan), ctypes.byref(bad))
+    return rc, (plan.value if rc == 0 else None), bad.value
+
+
+def cg_plan_run(plan, stream=None) -> int:
+    return library().cg_plan_run(plan, _stream(stream))
+
+
+def cg_plan_info(plan):
+    prec = ctypes.c_int32()
+    nb = ctypes.c_int32()
+    rc = library().cg_plan_info(plan, ctypes.byref(prec), ctypes.byref(nb))
+    return rc, prec.value, nb.value
+
+
+def cg_plan_destroy(plan) -> int:
+    return library().cg_plan_destroy(plan)
+
+
+def desc(op, B, U, R, K, N0, H, inp, out, qam_bits=2, Es=1.0, sinr_mode=0, normalize=0,
+         mu=None, rho=None, aux=None, status=None, n_inst=None) -> CgDesc:
+    """A CgDesc over tensors (n_inst defaults to H.shape[0])."""
+    n = int(H.shape[0]) if n_inst is None else int(n_inst)
+    return CgDesc(int(op), int(B), int(U), int(R), int(K), int(qam_bits), int(sinr_mode),
+                  int(normalize), float(N0), float(Es), n, _ptr(H), _ptr(inp), _ptr(out),
+                  _ptr(mu), _ptr(rho), _ptr(aux), _ptr(status))
 
 
 # ---------------------------------------------------------------------------

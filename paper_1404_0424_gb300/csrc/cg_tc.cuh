@@ -20,6 +20,7 @@
 #include <cuda_fp16.h>
 
 #include "cg_kernels.cuh"
+#include "cgmimo.h"
 
 namespace cgm {
 
@@ -158,7 +159,7 @@ __host__ __device__ inline TcPlan tc_detect_plan(int B, int U, int R, int exact)
   s.Kd = off; off += RMAX * 4;
   s.Nrm = off; off += RMAX * 4;
   s.misc = align16(off);
-  s.total = s.misc + 16;
+  s.total = s.misc + 32;  // mbarrier, status word, claimed work index
   return s;
 }
 
@@ -182,8 +183,122 @@ __host__ __device__ inline TcPlan tc_precode_plan(int B, int U, int R) {
   s.Kd = off; off += RMAX * 4;
   s.Nrm = off; off += RMAX * 4;
   s.misc = align16(off);
-  s.total = s.misc + 16;
+  s.total = s.misc + 32;  // mbarrier, status word, claimed work index
   return s;
+}
+
+// ---------------------------------------------------------------------------
+// Work sources: where a CTA finds its next instance and that instance's
+// parameters and buffers
+// ---------------------------------------------------------------------------
+
+struct DetItem {
+  const float2* H;
+  const float2* Y;
+  float2* xhat;
+  float* mu;
+  float* rho;
+  float* llr;
+  int32_t* status;
+  int B, U, R, K, q, exact, bulk;
+  float N0, Es, sigma;
+};
+
+struct PreItem {
+  const float2* H;
+  const float2* T;
+  float2* q;
+  float* qnorm;
+  int32_t* status;
+  int B, U, R, K, normalize, bulk_h, bulk_t;
+  float sigma;
+};
+
+__device__ __forceinline__ bool aligned16(const void* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
+// Work units (problem, instance) of one bin, claimed from a device counter.
+struct BatchArgs {
+  const cg_desc* desc;            // device copy of the plan's descriptors
+  const int2* work;               // (descriptor index, instance) of each unit in this bin
+  int64_t n_work;
+  unsigned long long* counter;    // claim counter, zero at launch
+  int PB, PR, PEX;                // plan shape of the bin: max B, max R, any exact tracker
+};
+
+__device__ __forceinline__ DetItem det_item(const DetectArgs& a, int64_t n) {
+  DetItem it;
+  it.H = a.H + n * a.B * a.U;
+  it.Y = a.Y + n * a.R * a.B;
+  const int64_t o = n * a.R * a.U;
+  it.xhat = a.xhat ? a.xhat + o : nullptr;
+  it.mu = a.mu ? a.mu + o : nullptr;
+  it.rho = a.rho ? a.rho + o : nullptr;
+  it.llr = a.llr ? a.llr + o * a.q : nullptr;
+  it.status = a.status ? a.status + n : nullptr;
+  it.B = a.B; it.U = a.U; it.R = a.R; it.K = a.K; it.q = a.q; it.exact = a.exact;
+  it.bulk = a.bulk;
+  it.N0 = a.N0; it.Es = a.Es; it.sigma = a.sigma;
+  return it;
+}
+
+__device__ __forceinline__ DetItem det_item(const BatchArgs& b, int64_t w) {
+  const int2 wu = b.work[w];
+  const cg_desc& d = b.desc[wu.x];
+  const int64_t n = wu.y;
+  DetItem it;
+  it.B = d.B; it.U = d.U; it.R = d.R; it.K = d.K; it.q = d.qam_bits;
+  it.exact = d.sinr_mode == 1;
+  it.N0 = d.N0; it.Es = d.Es; it.sigma = d.N0 / d.Es;
+  it.H = static_cast<const float2*>(d.H) + n * d.B * d.U;
+  it.Y = static_cast<const float2*>(d.in) + n * d.R * d.B;
+  const int64_t o = n * d.R * d.U;
+  it.xhat = d.out ? static_cast<float2*>(d.out) + o : nullptr;
+  it.mu = d.mu ? d.mu + o : nullptr;
+  it.rho = d.rho ? d.rho + o : nullptr;
+  it.llr = d.aux ? d.aux + o * d.qam_bits : nullptr;
+  it.status = d.status ? d.status + n : nullptr;
+  it.bulk = (d.B % 2 == 0) && aligned16(it.H) && aligned16(it.Y);
+  return it;
+}
+
+__device__ __forceinline__ PreItem pre_item(const PrecodeArgs& a, int64_t n) {
+  PreItem it;
+  it.H = a.H + n * a.B * a.U;
+  it.T = a.T + n * a.R * a.U;
+  it.q = a.q + n * a.R * a.B;
+  it.qnorm = a.qnorm ? a.qnorm + n * a.R : nullptr;
+  it.status = a.status ? a.status + n : nullptr;
+  it.B = a.B; it.U = a.U; it.R = a.R; it.K = a.K; it.normalize = a.normalize;
+  it.bulk_h = a.bulk_h; it.bulk_t = a.bulk_t; it.sigma = a.sigma;
+  return it;
+}
+
+__device__ __forceinline__ PreItem pre_item(const BatchArgs& b, int64_t w) {
+  const int2 wu = b.work[w];
+  const cg_desc& d = b.desc[wu.x];
+  const int64_t n = wu.y;
+  PreItem it;
+  it.B = d.B; it.U = d.U; it.R = d.R; it.K = d.K; it.normalize = d.normalize;
+  it.sigma = d.N0 / d.Es;
+  it.H = static_cast<const float2*>(d.H) + n * d.B * d.U;
+  it.T = static_cast<const float2*>(d.in) + n * d.R * d.U;
+  it.q = static_cast<float2*>(d.out) + n * d.R * d.B;
+  it.qnorm = d.aux ? d.aux + n * d.R : nullptr;
+  it.status = d.status ? d.status + n : nullptr;
+  it.bulk_h = ((d.B * d.U) % 2 == 0) && aligned16(it.H);
+  it.bulk_t = ((d.R * d.U) % 2 == 0) && aligned16(it.T);
+  return it;
+}
+
+// Claims the next work unit of a batch: thread 0 bumps the counter and
+// publishes the index in shared memory; readers wait for the next barrier.
+__device__ __forceinline__ void claim_next(const BatchArgs& b, int64_t* slot) {
+  if (threadIdx.x == 0) {
+    const unsigned long long w = atomicAdd(b.counter, 1ull);
+    *slot = w < static_cast<unsigned long long>(b.n_work) ? static_cast<int64_t>(w) : -1;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -745,13 +860,26 @@ struct TcCg {
 // CG-D, tensor-core variant
 // ---------------------------------------------------------------------------
 
-template <int UT, int EL, bool X3, bool FULL>
-__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
-    detect_tc_kernel(const DetectArgs a) {
+// Work source traits: DetectArgs / PrecodeArgs describe one shape for the
+// whole launch (instances taken by grid stride); BatchArgs hands out
+// (problem, instance) units of uneven shapes from a device counter.
+template <class S> struct SrcTraits;
+template <> struct SrcTraits<DetectArgs> { static constexpr bool kDyn = false; };
+template <> struct SrcTraits<PrecodeArgs> { static constexpr bool kDyn = false; };
+template <> struct SrcTraits<BatchArgs> { static constexpr bool kDyn = true; };
+
+__device__ __forceinline__ int64_t src_count(const DetectArgs& a) { return a.n_inst; }
+__device__ __forceinline__ int64_t src_count(const PrecodeArgs& a) { return a.n_inst; }
+__device__ __forceinline__ int64_t src_count(const BatchArgs& b) { return b.n_work; }
+
+template <int UT, int EL, bool X3, bool FULL, class Src>
+__device__ __forceinline__ void detect_tc_body(const Src& src, int PB, int PU, int PR,
+                                               int PEX) {
   using C = TcCfg<UT>;
-  constexpr int NTHR = C::NTHR, WM = C::WM, WK = C::WK, NT = C::NTD, SP = C::SP;
+  constexpr int NTHR = C::NTHR, WM = C::WM, WK = C::WK, NT = C::NTD;
+  constexpr bool kDyn = SrcTraits<Src>::kDyn;
   extern __shared__ __align__(128) unsigned char smem[];
-  const TcPlan P = tc_detect_plan<UT>(a.B, a.U, a.R, a.exact);
+  const TcPlan P = tc_detect_plan<UT>(PB, PU, PR, PEX);
   const float2* sHf = reinterpret_cast<const float2*>(smem + P.H);
   const float2* sYf = reinterpret_cast<const float2*>(smem + P.Y);
   float* part = reinterpret_cast<float*>(smem + P.Part);
@@ -763,43 +891,56 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
   float* sMu = reinterpret_cast<float*>(smem + P.Mu);
   float* sRho = reinterpret_cast<float*>(smem + P.Rho);
   float* sGd = reinterpret_cast<float*>(smem + P.Gd);
-  float* sAB = a.exact ? reinterpret_cast<float*>(smem + P.AB) : nullptr;
   int* sKd = reinterpret_cast<int*>(smem + P.Kd);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + P.misc);
   int* sStatus = reinterpret_cast<int*>(smem + P.misc + 8);
+  int64_t* sClaim = reinterpret_cast<int64_t*>(smem + P.misc + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, t = lane & 3;
-  const int U = a.U, R = a.R, B = a.B, Nz = U + R;
+  const int64_t count = src_count(src);
+
+  auto issue = [&](const DetItem& it) {
+    const uint32_t hb = uint32_t(it.B) * it.U * 8u, yb = uint32_t(it.B) * 8u;
+    mbar_arrive_expect_tx(bar, hb + uint32_t(it.R) * yb);
+    bulk_copy_g2s(smem + P.H, it.H, hb, bar);
+    for (int r = 0; r < it.R; ++r)
+      bulk_copy_g2s(smem + P.Y + uint32_t(r) * P.YS * 8u, it.Y + r * it.B, yb, bar);
+  };
 
   if (tid == 0) mbar_init(bar, 1);
-  __syncthreads();
+  int64_t cur;
+  if constexpr (kDyn) {
+    claim_next(src, sClaim);
+    __syncthreads();
+    cur = *sClaim;
+  } else {
+    __syncthreads();
+    cur = blockIdx.x < count ? int64_t(blockIdx.x) : -1;
+  }
   uint32_t parity = 0;
-  int64_t n = blockIdx.x;
-  auto issue = [&](int64_t inst) {
-    const uint32_t hb = uint32_t(B) * U * 8u, yb = uint32_t(B) * 8u;
-    mbar_arrive_expect_tx(bar, hb + uint32_t(R) * yb);
-    bulk_copy_g2s(smem + P.H, a.H + inst * B * U, hb, bar);
-    for (int r = 0; r < R; ++r)
-      bulk_copy_g2s(smem + P.Y + uint32_t(r) * P.YS * 8u, a.Y + (inst * R + r) * B, yb, bar);
-  };
-  if (a.bulk && n < a.n_inst && tid == 0) issue(n);
+  DetItem it{};
+  if (cur >= 0) {
+    it = det_item(src, cur);
+    if (it.bulk && tid == 0) issue(it);
+  }
 
-  for (; n < a.n_inst; n += gridDim.x) {
+  while (cur >= 0) {
+    const int U = it.U, R = it.R, B = it.B;
     // ---- step 1: FP32 inputs in shared memory
-    if (a.bulk) {
+    if (it.bulk) {
       if (!wait_inputs(bar, parity)) {
-        if (tid == 0 && a.status) a.status[n] = ST_TIMEOUT;
+        if (tid == 0 && it.status) *it.status = ST_TIMEOUT;
         mbar_wait_bounded(bar, parity, WAIT_TIMEOUT_NS);
         return;
       }
       parity ^= 1u;
     } else {
       float2* f = reinterpret_cast<float2*>(smem);
-      for (int e = tid; e < B * U; e += NTHR) f[e] = a.H[n * B * U + e];
+      for (int e = tid; e < B * U; e += NTHR) f[e] = it.H[e];
       float2* fy = reinterpret_cast<float2*>(smem + P.Y);
       for (int e = tid; e < R * B; e += NTHR) {
         const int r = e / B, b = e - r * B;
-        fy[r * P.YS + b] = a.Y[n * R * B + e];
+        fy[r * P.YS + b] = it.Y[e];
       }
       __syncthreads();
     }
@@ -818,16 +959,25 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
         part[((warp * NT + nt) * 8 + 4 + d) * 32 + lane] = Ci[nt][d];
       }
     __syncthreads();
-    tc_reduce_warp<UT, EL, NT>(part, WK, U, R, a.sigma, sA, sAc, sBm, sGd);
+    tc_reduce_warp<UT, EL, NT>(part, WK, U, R, it.sigma, sA, sAc, sBm, sGd);
     tc_zero_padding<UT>(U, R, sA, sAc, sBm, sGd, NTHR);
+    if constexpr (kDyn) claim_next(src, sClaim);
     __syncthreads();
-    const int64_t next = n + gridDim.x;
-    if (a.bulk && !a.exact && next < a.n_inst && tid == 0) {
+    int64_t next;
+    if constexpr (kDyn) {
+      next = *sClaim;
+    } else {
+      next = cur + gridDim.x < count ? cur + gridDim.x : -1;
+    }
+    DetItem nit{};
+    if (next >= 0) nit = det_item(src, next);
+    if (next >= 0 && nit.bulk && !it.exact && tid == 0) {
       fence_proxy_async_smem();
-      issue(next);
+      issue(nit);
     }
 
     // ---- step 3: Algorithm 1 lines 7-16
+    float* sAB = it.exact ? reinterpret_cast<float*>(smem + P.AB) : nullptr;
     if (warp * 8 < R) {
       const int n0 = warp * 8;
       TcCg<UT, EL> cg;
@@ -840,7 +990,7 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
             const int i = mt * 16 + g + 8 * h, r = n0 + 2 * t + rr;
             cg.res[mt][h][rr] = (i < U && r < R) ? sBm[r * UT + i] : make_float2(0.f, 0.f);
           }
-      cg.run(sAc, sA, sP, n0, U, R, a.K, sAB);
+      cg.run(sAc, sA, sP, n0, U, R, it.K, sAB);
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
         const int r = n0 + 2 * t + rr;
@@ -853,7 +1003,7 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
             if (i < U) {
               sX[r * UT + i] = cg.v[mt][h][rr];
               sMu[r * UT + i] = cg.l1[mt][h][rr] * sGd[i];  // Eq. 12
-              sRho[r * UT + i] = sGd[i] / a.N0;             // Eq. 13
+              sRho[r * UT + i] = sGd[i] / it.N0;            // Eq. 13
             }
           }
         if (g == 0) {
@@ -865,36 +1015,56 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
     __syncthreads();
 
     // ---- step 4: exact SINR (Eq. 10)
-    if (a.exact) {
-      exact_tracker<UT, NTHR>(reinterpret_cast<float2*>(smem), sA, sAB, sKd, U, R, a.sigma,
-                              a.N0, a.Es, sMu, sRho);
+    if (it.exact) {
+      exact_tracker<UT, NTHR>(reinterpret_cast<float2*>(smem), sA, sAB, sKd, U, R, it.sigma,
+                              it.N0, it.Es, sMu, sRho);
       __syncthreads();
-      if (a.bulk && next < a.n_inst && tid == 0) {
+      if (next >= 0 && nit.bulk && tid == 0) {
         fence_proxy_async_smem();
-        issue(next);
+        issue(nit);
       }
     }
 
     // ---- step 5: outputs (x_hat, mu, rho, LLRs of Eq. 4)
-    write_detect_outputs<UT, NTHR>(a, n, sX, sMu, sRho, sStatus);
+    {
+      DetectArgs o{};
+      o.xhat = it.xhat; o.mu = it.mu; o.rho = it.rho; o.llr = it.llr;
+      o.U = U; o.R = R; o.q = it.q; o.Es = it.Es;
+      write_detect_outputs<UT, NTHR>(o, 0, sX, sMu, sRho, sStatus);
+    }
     __syncthreads();
-    if (tid == 0 && a.status) a.status[n] = *sStatus;
-    (void)SP;
+    if (tid == 0 && it.status) *it.status = *sStatus;
+    cur = next;
+    it = nit;
   }
+}
+
+template <int UT, int EL, bool X3, bool FULL>
+__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
+    detect_tc_kernel(const DetectArgs a) {
+  detect_tc_body<UT, EL, X3, FULL>(a, a.B, a.U, a.R, a.exact);
+}
+
+// Batched form: one bin of uneven problems; the plan shape (PB, UT, PR, PEX)
+// bounds every problem of the bin, so the shared-memory layout is fixed.
+template <int UT, int EL, bool X3, bool FULL>
+__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
+    detect_tc_batch_kernel(const BatchArgs b) {
+  detect_tc_body<UT, EL, X3, FULL>(b, b.PB, UT, b.PR, b.PEX);
 }
 
 // ---------------------------------------------------------------------------
 // CG-P, tensor-core variant
 // ---------------------------------------------------------------------------
 
-template <int UT, int EL, bool X3, bool FULL>
-__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
-    precode_tc_kernel(const PrecodeArgs a) {
+template <int UT, int EL, bool X3, bool FULL, class Src>
+__device__ __forceinline__ void precode_tc_body(const Src& src, int PB, int PU, int PR) {
   using C = TcCfg<UT>;
   constexpr int NTHR = C::NTHR, NWARP = C::NWARP, WM = C::WM, WK = C::WK, NT = C::NTP;
   constexpr int SP = C::SP, KSV = C::KSC;
+  constexpr bool kDyn = SrcTraits<Src>::kDyn;
   extern __shared__ __align__(128) unsigned char smem[];
-  const TcPlan P = tc_precode_plan<UT>(a.B, a.U, a.R);
+  const TcPlan P = tc_precode_plan<UT>(PB, PU, PR);
   const uint2* Hc = reinterpret_cast<const uint2*>(smem + P.H);
   const float2* sT = reinterpret_cast<const float2*>(smem + P.Y);
   float* part = reinterpret_cast<float*>(smem + P.Part);
@@ -905,15 +1075,27 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
   float* sGd = reinterpret_cast<float*>(smem + P.Gd);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + P.misc);
   int* sStatus = reinterpret_cast<int*>(smem + P.misc + 8);
+  int64_t* sClaim = reinterpret_cast<int64_t*>(smem + P.misc + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, t = lane & 3;
-  const int U = a.U, R = a.R, B = a.B;
-  const bool bulk = a.bulk_h || a.bulk_t;
+  const int64_t count = src_count(src);
 
   if (tid == 0) mbar_init(bar, 1);
-  __syncthreads();
+  int64_t n;
+  if constexpr (kDyn) {
+    claim_next(src, sClaim);
+    __syncthreads();
+    n = *sClaim;
+  } else {
+    __syncthreads();
+    n = blockIdx.x < count ? int64_t(blockIdx.x) : -1;
+  }
   uint32_t parity = 0;
-  for (int64_t n = blockIdx.x; n < a.n_inst; n += gridDim.x) {
+  while (n >= 0) {
+    const PreItem a = pre_item(src, n);
+    const int U = a.U, R = a.R, B = a.B;
+    const int B8 = (B + 7) & ~7;  // this problem's padded antenna count (layout uses P)
+    const bool bulk = a.bulk_h || a.bulk_t;
     // ---- step 1: inputs
     if (bulk && tid == 0) {
       fence_proxy_async_smem();
@@ -921,20 +1103,20 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
       if (a.bulk_h) bytes += uint32_t(B) * U * 8u;
       if (a.bulk_t) bytes += uint32_t(R) * U * 8u;
       mbar_arrive_expect_tx(bar, bytes);
-      if (a.bulk_h) bulk_copy_g2s(smem + P.H, a.H + n * B * U, uint32_t(B) * U * 8u, bar);
-      if (a.bulk_t) bulk_copy_g2s(smem + P.Y, a.T + n * R * U, uint32_t(R) * U * 8u, bar);
+      if (a.bulk_h) bulk_copy_g2s(smem + P.H, a.H, uint32_t(B) * U * 8u, bar);
+      if (a.bulk_t) bulk_copy_g2s(smem + P.Y, a.T, uint32_t(R) * U * 8u, bar);
     }
     if (!a.bulk_h) {
       float2* f = reinterpret_cast<float2*>(smem + P.H);
-      for (int e = tid; e < B * U; e += NTHR) f[e] = a.H[n * B * U + e];
+      for (int e = tid; e < B * U; e += NTHR) f[e] = a.H[e];
     }
     if (!a.bulk_t) {
       float2* f = reinterpret_cast<float2*>(smem + P.Y);
-      for (int e = tid; e < R * U; e += NTHR) f[e] = a.T[n * R * U + e];
+      for (int e = tid; e < R * U; e += NTHR) f[e] = a.T[e];
     }
     if (bulk) {
       if (!wait_inputs(bar, parity)) {
-        if (tid == 0 && a.status) a.status[n] = ST_TIMEOUT;
+        if (tid == 0 && a.status) *a.status = ST_TIMEOUT;
         mbar_wait_bounded(bar, parity, WAIT_TIMEOUT_NS);
         return;
       }
@@ -948,11 +1130,11 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
     if (FULL)
       convert_h_full<EL, NTHR, UT>(smem + P.H, B);
     else
-      convert_h<EL, NTHR>(smem + P.H, B, P.B8, U);
+      convert_h<EL, NTHR>(smem + P.H, B, B8, U);
     __syncthreads();
     {
       float Cr[NT][4], Ci[NT][4];
-      tc_gram<UT, EL, X3, NT>(Hc, nullptr, 0, P.B8, U, U, warp % WM, warp / WM, WK, Cr, Ci);
+      tc_gram<UT, EL, X3, NT>(Hc, nullptr, 0, B8, U, U, warp % WM, warp / WM, WK, Cr, Ci);
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
@@ -1008,7 +1190,7 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
         if (g == 0 && r < R) {
           const float nr = sqrtf(fmaxf(qq, 0.f));
           sNrm[r] = nr;
-          if (a.qnorm) a.qnorm[n * R + r] = nr;
+          if (a.qnorm) a.qnorm[r] = nr;
           if (cg.broke[rr]) atomicOr(sStatus, ST_BREAKDOWN);
         }
       }
@@ -1052,7 +1234,7 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
             vh[nt][ks][reg][1] = swap_halves(sv.x);  // (vi, vr): imaginary part
             vl[nt][ks][reg][1] = swap_halves(sv.y);
           }
-      const int MTQ = (P.B8 + 15) / 16;
+      const int MTQ = (B8 + 15) / 16;
       for (int mt = warp; mt < MTQ; mt += NWARP) {
         const int r0 = mt * 16 + g, r1 = r0 + 8;  // antenna rows of this m-tile
         float Qr[2][4], Qi[2][4];
@@ -1065,10 +1247,10 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
           const int j0 = ks * 8 + t, j1 = j0 + 4;
           uint32_t ah[4], al[4];
           const uint2 z = make_uint2(0u, 0u);
-          const uint2 x0 = (r0 < P.B8 && j0 < U) ? Hc[r0 * U + (j0 ^ hswz(r0, U))] : z;
-          const uint2 x1 = (r1 < P.B8 && j0 < U) ? Hc[r1 * U + (j0 ^ hswz(r1, U))] : z;
-          const uint2 x2 = (r0 < P.B8 && j1 < U) ? Hc[r0 * U + (j1 ^ hswz(r0, U))] : z;
-          const uint2 x3 = (r1 < P.B8 && j1 < U) ? Hc[r1 * U + (j1 ^ hswz(r1, U))] : z;
+          const uint2 x0 = (r0 < B8 && j0 < U) ? Hc[r0 * U + (j0 ^ hswz(r0, U))] : z;
+          const uint2 x1 = (r1 < B8 && j0 < U) ? Hc[r1 * U + (j0 ^ hswz(r1, U))] : z;
+          const uint2 x2 = (r0 < B8 && j1 < U) ? Hc[r0 * U + (j1 ^ hswz(r0, U))] : z;
+          const uint2 x3 = (r1 < B8 && j1 < U) ? Hc[r1 * U + (j1 ^ hswz(r1, U))] : z;
           ah[0] = x0.x; al[0] = x0.y;
           ah[1] = x1.x; al[1] = x1.y;
           ah[2] = x2.x; al[2] = x2.y;
@@ -1098,15 +1280,33 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
                 val.x *= inv;
                 val.y *= inv;
               }
-              a.q[(n * R + r) * B + b] = val;
+              a.q[r * B + b] = val;
             }
           }
         }
       }
     }
+    if constexpr (kDyn) claim_next(src, sClaim);
     __syncthreads();
-    if (tid == 0 && a.status) a.status[n] = *sStatus;
+    if (tid == 0 && a.status) *a.status = *sStatus;
+    if constexpr (kDyn) {
+      n = *sClaim;
+    } else {
+      n = n + gridDim.x < count ? n + gridDim.x : -1;
+    }
   }
+}
+
+template <int UT, int EL, bool X3, bool FULL>
+__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
+    precode_tc_kernel(const PrecodeArgs a) {
+  precode_tc_body<UT, EL, X3, FULL>(a, a.B, a.U, a.R);
+}
+
+template <int UT, int EL, bool X3, bool FULL>
+__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
+    precode_tc_batch_kernel(const BatchArgs b) {
+  precode_tc_body<UT, EL, X3, FULL>(b, b.PB, UT, b.PR);
 }
 
 }  // namespace cgm

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "cg_kernels.cuh"
+#include "cg_tc.cuh"
 
 namespace cgm {
 
@@ -30,6 +31,12 @@ cudaError_t launch_precode_tc(int UT, int el, bool x3, const PrecodeArgs& a, cud
                               int* grid_out);
 uint32_t tc_detect_smem_bytes(int UT, int B, int U, int R, int exact);
 uint32_t tc_precode_smem_bytes(int UT, int B, int U, int R);
+
+// Batched tensor-core kernels (tc.cu): op 0 = detect, 1 = precode. With
+// launch = false only the launch shape is computed (smem bytes, grid).
+cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const BatchArgs& b,
+                            int max_grid, cudaStream_t s, bool launch, uint32_t* smem_out,
+                            int* grid_out);
 
 // Dynamic shared memory of one CTA for the given shape (bytes).
 uint32_t detect_smem_bytes(int UT, int B, int U, int R, int exact);

@@ -141,3 +141,70 @@ cudaError_t launch_precode_tc(int UT, int el, bool x3, const PrecodeArgs& a, cud
 }
 
 }  // namespace cgm
+
+// ---------------------------------------------------------------------------
+// Batched (plan) kernels
+// ---------------------------------------------------------------------------
+
+namespace cgm {
+
+namespace {
+
+template <int UT, int EL, bool X3, bool FULL>
+cudaError_t batch_t(int op, const BatchArgs& b, int max_grid, cudaStream_t s, bool launch,
+                    uint32_t* smem_out, int* grid_out) {
+  constexpr int NTHR = TcCfg<UT>::NTHR;
+  const uint32_t smem = op == 0 ? tc_detect_plan<UT>(b.PB, UT, b.PR, b.PEX).total
+                                : tc_precode_plan<UT>(b.PB, UT, b.PR).total;
+  int slots = 0;
+  const uint64_t id = (op == 0 ? 0x4000 : 0x8000) | (UT << 3) | (EL << 2) | (X3 ? 2 : 0) |
+                      (FULL ? 1 : 0);
+  cudaError_t err = op == 0
+                        ? prepare(detect_tc_batch_kernel<UT, EL, X3, FULL>, id, NTHR, smem, &slots)
+                        : prepare(precode_tc_batch_kernel<UT, EL, X3, FULL>, id, NTHR, smem, &slots);
+  if (err != cudaSuccess) return err;
+  int64_t grid = slots < b.n_work ? slots : b.n_work;
+  if (max_grid > 0 && grid > max_grid) grid = max_grid;
+  if (grid < 1) grid = 1;
+  if (smem_out) *smem_out = smem;
+  if (grid_out) *grid_out = int(grid);
+  if (!launch) return cudaSuccess;
+  if (op == 0)
+    detect_tc_batch_kernel<UT, EL, X3, FULL><<<unsigned(grid), NTHR, smem, s>>>(b);
+  else
+    precode_tc_batch_kernel<UT, EL, X3, FULL><<<unsigned(grid), NTHR, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+template <int UT, int EL, bool X3>
+cudaError_t batch_f(int op, bool full, const BatchArgs& b, int mg, cudaStream_t s, bool l,
+                    uint32_t* sm, int* g) {
+  return full ? batch_t<UT, EL, X3, true>(op, b, mg, s, l, sm, g)
+              : batch_t<UT, EL, X3, false>(op, b, mg, s, l, sm, g);
+}
+
+template <int UT>
+cudaError_t batch_ut(int op, int el, bool x3, bool full, const BatchArgs& b, int mg,
+                     cudaStream_t s, bool l, uint32_t* sm, int* g) {
+  if (el == EL_BF16)
+    return x3 ? batch_f<UT, EL_BF16, true>(op, full, b, mg, s, l, sm, g)
+              : batch_f<UT, EL_BF16, false>(op, full, b, mg, s, l, sm, g);
+  return x3 ? batch_f<UT, EL_F16, true>(op, full, b, mg, s, l, sm, g)
+            : batch_f<UT, EL_F16, false>(op, full, b, mg, s, l, sm, g);
+}
+
+}  // namespace
+
+cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const BatchArgs& b,
+                            int max_grid, cudaStream_t s, bool launch, uint32_t* smem_out,
+                            int* grid_out) {
+  switch (UT) {
+    case 4:
+    case 8: return batch_ut<8>(op, el, x3, full, b, max_grid, s, launch, smem_out, grid_out);
+    case 16: return batch_ut<16>(op, el, x3, full, b, max_grid, s, launch, smem_out, grid_out);
+    case 32: return batch_ut<32>(op, el, x3, full, b, max_grid, s, launch, smem_out, grid_out);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace cgm

@@ -87,3 +87,18 @@ def test_precode_rejects_invalid_arguments(lib):
     assert cabi.cg_precode(p, 1, 16, 16, 16) == cabi.CG_EINVAL
     assert cabi.cg_precode_host(p, 1, 16, 16, 16) == cabi.CG_EINVAL
     assert cabi.cg_precode(cabi.params(**GOOD), 0, None, None, None) == cabi.CG_OK
+
+
+def test_plan_rejects_invalid_descriptors_on_the_host(lib):
+    good = cabi.CgDesc(0, 32, 4, 1, 3, 4, 0, 0, 0.5, 1.0, 1, 16, 16, 16, None, None, None, None)
+    bad_k = cabi.CgDesc(0, 32, 4, 1, 5, 4, 0, 0, 0.5, 1.0, 1, 16, 16, 16, None, None, None, None)
+    bad_op = cabi.CgDesc(7, 32, 4, 1, 3, 4, 0, 0, 0.5, 1.0, 1, 16, 16, 16, None, None, None, None)
+    no_q = cabi.CgDesc(1, 32, 4, 1, 3, 4, 0, 0, 0.5, 1.0, 1, 16, 16, None, None, None, None, None)
+    neg_n = cabi.CgDesc(0, 32, 4, 1, 3, 4, 0, 0, 0.5, 1.0, -2, 16, 16, 16, None, None, None, None)
+    for descs, idx in (([good, bad_k], 1), ([bad_op], 0), ([good, good, no_q], 2), ([neg_n], 0)):
+        rc, plan, bad = cabi.cg_plan_create(descs, 4)
+        assert rc == cabi.CG_EINVAL and plan is None and bad == idx
+    assert cabi.cg_plan_create([good], 0)[0] == cabi.CG_ENOTSUP     # FP32 plans: no
+    assert cabi.cg_plan_create([good], 9)[0] == cabi.CG_EINVAL
+    assert lib.cg_plan_run(None, None) == cabi.CG_EINVAL
+    assert lib.cg_plan_destroy(None) == cabi.CG_EINVAL

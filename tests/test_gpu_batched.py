@@ -1,0 +1,174 @@
+"""Batched uneven problems (cg_plan_*): each problem's result inside a mixed
+batch equals the single-shape call bit for bit, and a sample matches the
+FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1404_0424_gb300 import workload as wl
+from tests.parity import check_detect, check_precode, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cabi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_0424_gb300 import build, cabi as c
+    c.library(build.build())
+    return c
+
+
+SHAPES = [(64, 8), (128, 16), (128, 32), (256, 32), (100, 12), (33, 5), (48, 3), (72, 24)]
+
+
+def make_batch(n_prob, seed, dev, exact_every=5):
+    rng = np.random.default_rng(seed)
+    probs = []
+    for k in range(n_prob):
+        B, U = SHAPES[rng.integers(len(SHAPES))]
+        q = int(rng.choice([4, 6, 8]))
+        R = int(rng.integers(1, 15))
+        K = int(max(1, min(U // 4, 8)))
+        snr = float(rng.uniform(5, 25))
+        n = int(rng.integers(1, 4))
+        op = int(rng.integers(2))
+        exact = int(op == 0 and k % exact_every == 0)
+        if op == 0:
+            d = wl.uplink(B, U, q, n=n, R=R, snr_db=snr, seed=seed * 1000 + k)
+            t = {"H": torch.from_numpy(d["H"]).to(dev), "Y": torch.from_numpy(d["Y"]).to(dev),
+                 "xhat": torch.full((n, R, U), np.nan, dtype=torch.complex64, device=dev),
+                 "mu": torch.full((n, R, U), np.nan, device=dev),
+                 "rho": torch.full((n, R, U), np.nan, device=dev),
+                 "llr": torch.full((n, R, U, q), np.nan, device=dev),
+                 "status": torch.full((n,), -1, dtype=torch.int32, device=dev)}
+        else:
+            d = wl.downlink(B, U, q, n=n, R=R, snr_db=snr, seed=seed * 1000 + k)
+            t = {"H": torch.from_numpy(d["H"]).to(dev), "T": torch.from_numpy(d["T"]).to(dev),
+                 "q": torch.full((n, R, B), np.nan, dtype=torch.complex64, device=dev),
+                 "qnorm": torch.full((n, R), np.nan, device=dev),
+                 "status": torch.full((n,), -1, dtype=torch.int32, device=dev)}
+        probs.append({"op": op, "B": B, "U": U, "R": R, "K": K, "q": q, "n": n, "exact": exact,
+                      "normalize": int(op == 1 and k % 3 == 0), "d": d, "t": t})
+    return probs
+
+
+def descs(cabi, probs):
+    out = []
+    for p in probs:
+        t = p["t"]
+        if p["op"] == 0:
+            out.append(cabi.desc(0, p["B"], p["U"], p["R"], p["K"], p["d"]["N0"], t["H"], t["Y"],
+                                 t["xhat"], qam_bits=p["q"], sinr_mode=p["exact"], mu=t["mu"],
+                                 rho=t["rho"], aux=t["llr"], status=t["status"]))
+        else:
+            out.append(cabi.desc(1, p["B"], p["U"], p["R"], p["K"], p["d"]["N0"], t["H"], t["T"],
+                                 t["q"], normalize=p["normalize"], aux=t["qnorm"],
+                                 status=t["status"]))
+    return out
+
+
+def single(cabi, p, precision):
+    t = p["t"]
+    if p["op"] == 0:
+        return cabi.detect(t["H"], t["Y"], p["d"]["N0"], p["K"], p["q"], sinr_mode=p["exact"],
+                           precision=precision)
+    return cabi.precode(t["H"], t["T"], p["d"]["N0"], p["K"], normalize=bool(p["normalize"]),
+                        precision=precision)
+
+
+@pytest.mark.parametrize("precision", [4, 3])
+def test_batch_equals_single_calls_bitwise(cabi, precision):
+    dev = torch.device("cuda:0")
+    probs = make_batch(40, seed=11 + precision, dev=dev)
+    rc, plan, bad = cabi.cg_plan_create(descs(cabi, probs), precision)
+    assert rc == 0, (cabi.cg_strerror(rc), bad)
+    try:
+        rc, prec, nbins = cabi.cg_plan_info(plan)
+        assert rc == 0 and prec == precision and nbins >= 4
+        assert cabi.cg_plan_run(plan) == 0
+        torch.cuda.synchronize()
+        first = [{k: v.clone() for k, v in p["t"].items()} for p in probs]
+        assert cabi.cg_plan_run(plan) == 0   # replay: same outputs
+        torch.cuda.synchronize()
+        for p, f in zip(probs, first):
+            ref = single(cabi, p, precision)
+            torch.cuda.synchronize()
+            keys = ("xhat", "mu", "rho", "llr", "status") if p["op"] == 0 else ("q", "qnorm",
+                                                                               "status")
+            for k in keys:
+                assert torch.equal(p["t"][k], f[k]), f"replay differs in {k}"
+                assert torch.equal(p["t"][k], ref[k]), (f"{k} differs from the single call for "
+                                                        f"{p['op'], p['B'], p['U'], p['R']}")
+    finally:
+        cabi.cg_plan_destroy(plan)
+
+
+def test_batch_matches_oracle(cabi):
+    dev = torch.device("cuda:0")
+    probs = make_batch(24, seed=5, dev=dev)
+    rc, plan, bad = cabi.cg_plan_create(descs(cabi, probs), 4)
+    assert rc == 0, (cabi.cg_strerror(rc), bad)
+    try:
+        assert cabi.cg_plan_run(plan) == 0
+        torch.cuda.synchronize()
+    finally:
+        cabi.cg_plan_destroy(plan)
+    for p in probs:
+        d = p["d"]
+        t = p["t"]
+        if p["op"] == 0:
+            r = oracle.cg_detect(d["H"], d["Y"], d["N0"], 1.0, p["K"], p["q"],
+                                 "exact" if p["exact"] else "approx")
+            check_detect({k: to_np(t[k]) for k in ("xhat", "mu", "rho", "llr", "status")}, r)
+        else:
+            r = oracle.cg_precode(d["H"], d["T"], d["N0"], 1.0, p["K"])
+            check_precode({k: to_np(t[k]) for k in ("q", "qnorm", "status")}, r,
+                          normalize=bool(p["normalize"]))
+
+
+def test_auto_precision_and_config_batch(cabi):
+    # 4096 problems drawn like the uneven-batch workload; AUTO picks a split mode
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(3)
+    shapes = [(64, 8), (128, 16), (128, 32), (256, 32)]
+    probs = []
+    n = 4096
+    keep = []
+    for k in range(n):
+        B, U = shapes[rng.integers(4)]
+        R = int(rng.integers(1, 15))
+        q = int(rng.choice([4, 6, 8]))
+        probs.append((B, U, R, q, float(rng.uniform(5, 25))))
+    ds = []
+    for k, (B, U, R, q, snr) in enumerate(probs):
+        H = torch.randn((1, B, U), dtype=torch.complex64, device=dev)
+        Y = torch.randn((1, R, B), dtype=torch.complex64, device=dev)
+        out = {"xhat": torch.empty((1, R, U), dtype=torch.complex64, device=dev),
+               "mu": torch.empty((1, R, U), device=dev), "rho": torch.empty((1, R, U), device=dev),
+               "llr": torch.empty((1, R, U, q), device=dev),
+               "status": torch.empty((1,), dtype=torch.int32, device=dev)}
+        keep.append((H, Y, out))
+        ds.append(cabi.desc(0, B, U, R, max(1, min(U // 4, 8)), wl.snr_to_n0(snr, U), H, Y,
+                            out["xhat"], qam_bits=q, mu=out["mu"], rho=out["rho"],
+                            aux=out["llr"], status=out["status"]))
+    rc, plan, bad = cabi.cg_plan_create(ds, -1)
+    assert rc == 0, (cabi.cg_strerror(rc), bad)
+    try:
+        rc, prec, nb = cabi.cg_plan_info(plan)
+        assert prec in (3, 4) and nb == 3   # (128,32) and (256,32) share the UT=32 bin
+        assert cabi.cg_plan_run(plan) == 0
+        torch.cuda.synchronize()
+        assert all(int(o["status"][0]) == 0 for _, _, o in keep)
+        for idx in (0, 17, 999, 4095):
+            H, Y, o = keep[idx]
+            B, U, R, q, snr = probs[idx]
+            r = oracle.cg_detect(H.cpu().numpy(), Y.cpu().numpy(), wl.snr_to_n0(snr, U), 1.0,
+                                 max(1, min(U // 4, 8)), q)
+            check_detect({k: to_np(v) for k, v in o.items()}, r)
+    finally:
+        cabi.cg_plan_destroy(plan)
