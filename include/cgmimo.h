@@ -56,6 +56,7 @@ extern "C" {
 #define CG_EAGAIN (-4)     /* resource temporarily full (serving queue) */
 #define CG_ETIMEDOUT (-5)  /* a bounded wait expired */
 #define CG_ENOTSUP (-6)    /* valid but unsupported combination of modes */
+#define CG_ETOOBIG (-7)    /* request exceeds a fixed capacity (cg_batch_run_static) */
 
 /* Per-instance status bits. */
 #define CG_STATUS_BREAKDOWN 1  /* CG stopped before K: ||r_{k-1}||^2 or Re(p^H A p) not > 0 */
@@ -188,6 +189,45 @@ int cg_plan_info(const cg_plan* plan, int32_t* precision, int32_t* n_bins);
 
 /* Releases the plan (waits for its outstanding runs first). */
 int cg_plan_destroy(cg_plan* plan);
+
+/* ------------------------------------------------------------------------
+ * Batched problems without any allocation
+ * ------------------------------------------------------------------------ */
+
+/* Capacity of cg_batch_run_static per call. */
+#define CG_STATIC_MAX_PROBLEMS 4096
+#define CG_STATIC_MAX_INSTANCES 65536
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * are not allowed to allocate. A real-time receiver that runs detection
+ * once per slot under a sub-millisecond deadline cannot call cudaMalloc or
+ * cudaFree in that loop: both may synchronise the device and take unbounded
+ * time, so such code allocates everything at start-up. Code that works
+ * inside a device-memory budget owned by another allocator is in the same
+ * position. cg_plan_create keeps its work tables in memory it allocates;
+ * this call runs the same batched kernels with those tables in a static
+ * device array of the library instead (about 1 MiB, held by every GPU that
+ * loads the library until the process exits), and it calls no allocating
+ * routine.
+ *
+ * Arguments: descs is a HOST array of n problems with the meaning of
+ * cg_desc; all buffers they name are caller-provided DEVICE memory.
+ * precision is CG_PREC_BF16, CG_PREC_FP16, CG_PREC_BF16X3 or
+ * CG_PREC_FP16X3 (no autotuning). Work is enqueued on `stream`; the call
+ * returns once the descriptor copy is queued, and the host array may be
+ * reused at once.
+ *
+ * Limits: more than CG_STATIC_MAX_PROBLEMS problems or more than
+ * CG_STATIC_MAX_INSTANCES instances in total returns CG_ETOOBIG with no
+ * work enqueued; invalid descriptors return CG_EINVAL.
+ *
+ * The first call on a device looks up the device address of the static
+ * array on that device (make the device current first); make that first
+ * call before any stream capture. Every call reuses the same array, which
+ * keeps the previous call's contents; the call resets the parts that must
+ * start at zero. Calls whose work overlaps on the GPU (different streams,
+ * or other threads) race on the array: order them on one stream. */
+int cg_batch_run_static(const cg_desc* descs, int64_t n, int32_t precision, void* stream);
 
 /* Frees the workspace of the *_host calls on the current device. */
 int cg_release_workspace(void);

@@ -75,6 +75,7 @@ _SIGS = {
     "cg_plan_run": [_VP, _VP],
     "cg_plan_info": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "cg_plan_destroy": [_VP],
+    "cg_batch_run_static": [ctypes.POINTER(CgDesc), ctypes.c_int64, ctypes.c_int32, _VP],
     "cg_strerror": [ctypes.c_int],
     "cg_version": [],
 }
@@ -187,6 +188,12 @@ def cg_plan_info(plan):
 
 def cg_plan_destroy(plan) -> int:
     return library().cg_plan_destroy(plan)
+
+
+def cg_batch_run_static(descs, precision=4, stream=None) -> int:
+    """Batched problems through the allocation-free entry point (see cgmimo.h)."""
+    arr = (CgDesc * max(len(descs), 1))(*descs)
+    return library().cg_batch_run_static(arr, len(descs), int(precision), _stream(stream))
 
 
 def desc(op, B, U, R, K, N0, H, inp, out, qam_bits=2, Es=1.0, sinr_mode=0, normalize=0,

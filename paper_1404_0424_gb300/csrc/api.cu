@@ -316,6 +316,7 @@ const char* cg_strerror(int code) {
     case CG_EAGAIN: return "CG_EAGAIN: resource temporarily full";
     case CG_ETIMEDOUT: return "CG_ETIMEDOUT: bounded wait expired";
     case CG_ENOTSUP: return "CG_ENOTSUP: unsupported mode combination";
+    case CG_ETOOBIG: return "CG_ETOOBIG: request exceeds a fixed capacity";
     default: return "unknown cgmimo error code";
   }
 }
