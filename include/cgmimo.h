@@ -191,6 +191,69 @@ int cg_plan_info(const cg_plan* plan, int32_t* precision, int32_t* n_bins);
 int cg_plan_destroy(cg_plan* plan);
 
 /* ------------------------------------------------------------------------
+ * Serving: a device-resident request loop with continuous batching
+ * ------------------------------------------------------------------------ */
+
+/* Server configuration.
+ *   capacity          requests in flight at most (ring slots), >= 1
+ *   precision         CG_PREC_BF16, CG_PREC_FP16, CG_PREC_BF16X3 or CG_PREC_FP16X3
+ *   hbm_budget_bytes  admission limit: input + output bytes of admitted,
+ *                     unfinished requests (a request larger than it is CG_ETOOBIG)
+ *   max_B, max_R      largest B and R a request may have (they size the kernels)
+ *   ctas_per_class    persistent CTAs of each class kernel; 0 = an equal share of
+ *                     the resident CTAs among the six classes
+ *   idle_timeout_ms   a class kernel exits after this long without work and is
+ *                     relaunched by the next submit or poll that needs it          */
+typedef struct cg_serve_cfg {
+  int32_t capacity;
+  int32_t precision;
+  int64_t hbm_budget_bytes;
+  int32_t max_B, max_R;
+  int32_t ctas_per_class;
+  int32_t idle_timeout_ms;
+} cg_serve_cfg;
+
+/* Timing of one request. Host times are CLOCK_MONOTONIC nanoseconds; device
+ * times are the GPU global timer (nanoseconds, its own epoch). */
+typedef struct cg_req_stats {
+  int32_t status;           /* OR of the instances' CG_STATUS_* bits */
+  int32_t pad;
+  int64_t submit_ns;        /* host, cg_serve_submit accepted the request */
+  int64_t complete_ns;      /* host, first cg_serve_poll that saw it complete */
+  int64_t device_first_ns;  /* device, its first instance was claimed */
+  int64_t device_done_ns;   /* device, its last instance was finished */
+} cg_req_stats;
+
+typedef struct cg_server cg_server;
+
+/* Creates a server on the current device and starts nothing yet: the class
+ * kernels (detection or precoding x padded user count 8, 16, 32) launch on
+ * the first request of their class, each on its own stream. Requests are
+ * published through pinned, mapped host memory; a request's instances are
+ * claimed one at a time by any CTA of its class, oldest request first, so
+ * requests that arrive while others run are admitted as CTAs free up and
+ * their work overlaps on the device. Every device wait is bounded. */
+int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out);
+
+/* Non-blocking submit of one request (a cg_desc with n_inst >= 1 whose
+ * DEVICE buffers stay valid until it completes). Returns CG_EAGAIN when all
+ * ring slots are in use or admitting it would exceed the HBM budget (poll
+ * and retry), CG_EINVAL for an invalid request, CG_ETOOBIG when it alone
+ * exceeds the budget; on success *ticket identifies it. */
+int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket);
+
+/* *done = 1 once every instance of the request is finished and its outputs
+ * are visible to the host; stats (may be NULL) are filled when done. Poll a
+ * ticket before `capacity` newer requests are submitted (its slot is then
+ * reused and the call returns CG_EINVAL). */
+int cg_serve_poll(cg_server* s, uint64_t ticket, int32_t* done, cg_req_stats* stats);
+
+/* Stops the class kernels (bounded wait) and frees the server. Requests still
+ * in flight may not complete. Returns CG_ETIMEDOUT, leaving the server's
+ * memory allocated, if a kernel did not stop in time. */
+int cg_serve_destroy(cg_server* s);
+
+/* ------------------------------------------------------------------------
  * Batched problems without any allocation
  * ------------------------------------------------------------------------ */
 

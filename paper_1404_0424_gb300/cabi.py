@@ -49,6 +49,19 @@ class CgDesc(ctypes.Structure):
                 ("status", ctypes.c_void_p)]
 
 
+class CgServeCfg(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("max_B", ctypes.c_int32),
+                ("max_R", ctypes.c_int32), ("ctas_per_class", ctypes.c_int32),
+                ("idle_timeout_ms", ctypes.c_int32)]
+
+
+class CgReqStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("submit_ns", ctypes.c_int64), ("complete_ns", ctypes.c_int64),
+                ("device_first_ns", ctypes.c_int64), ("device_done_ns", ctypes.c_int64)]
+
+
 class CgError(RuntimeError):
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {cg_strerror(code)} ({code})")
@@ -76,6 +89,11 @@ _SIGS = {
     "cg_plan_info": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "cg_plan_destroy": [_VP],
     "cg_batch_run_static": [ctypes.POINTER(CgDesc), ctypes.c_int64, ctypes.c_int32, _VP],
+    "cg_serve_create": [ctypes.POINTER(CgServeCfg), ctypes.POINTER(ctypes.c_void_p)],
+    "cg_serve_submit": [_VP, ctypes.POINTER(CgDesc), ctypes.POINTER(ctypes.c_uint64)],
+    "cg_serve_poll": [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                      ctypes.POINTER(CgReqStats)],
+    "cg_serve_destroy": [_VP],
     "cg_strerror": [ctypes.c_int],
     "cg_version": [],
 }
@@ -194,6 +212,35 @@ def cg_batch_run_static(descs, precision=4, stream=None) -> int:
     """Batched problems through the allocation-free entry point (see cgmimo.h)."""
     arr = (CgDesc * max(len(descs), 1))(*descs)
     return library().cg_batch_run_static(arr, len(descs), int(precision), _stream(stream))
+
+
+def cg_serve_create(capacity=256, precision=4, hbm_budget_bytes=40 << 30, max_B=256, max_R=16,
+                    ctas_per_class=0, idle_timeout_ms=500):
+    """Returns (rc, server handle or None)."""
+    cfg = CgServeCfg(int(capacity), int(precision), int(hbm_budget_bytes), int(max_B),
+                     int(max_R), int(ctas_per_class), int(idle_timeout_ms))
+    srv = ctypes.c_void_p()
+    rc = library().cg_serve_create(ctypes.byref(cfg), ctypes.byref(srv))
+    return rc, (srv.value if rc == 0 else None)
+
+
+def cg_serve_submit(server, req: CgDesc):
+    """Returns (rc, ticket)."""
+    t = ctypes.c_uint64()
+    rc = library().cg_serve_submit(server, ctypes.byref(req), ctypes.byref(t))
+    return rc, t.value
+
+
+def cg_serve_poll(server, ticket):
+    """Returns (rc, done, CgReqStats)."""
+    done = ctypes.c_int32()
+    st = CgReqStats()
+    rc = library().cg_serve_poll(server, int(ticket), ctypes.byref(done), ctypes.byref(st))
+    return rc, done.value, st
+
+
+def cg_serve_destroy(server) -> int:
+    return library().cg_serve_destroy(server)
 
 
 def desc(op, B, U, R, K, N0, H, inp, out, qam_bits=2, Es=1.0, sinr_mode=0, normalize=0,

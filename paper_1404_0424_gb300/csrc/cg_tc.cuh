@@ -292,6 +292,147 @@ __device__ __forceinline__ PreItem pre_item(const BatchArgs& b, int64_t w) {
   return it;
 }
 
+// ---------------------------------------------------------------------------
+// Serving: requests published by the host, claimed instance by instance
+// ---------------------------------------------------------------------------
+
+// Device copy of one request (written by the host at submit) and its
+// progress counters.
+struct ServeSlot {
+  cg_desc d;
+  unsigned long long claim;   // next instance to hand out
+  unsigned long long done;    // instances finished
+  unsigned long long ticket;  // submit ticket of the request in this slot
+  int status;                 // OR of the instances' status words
+  int pad;
+};
+
+// Completion record in mapped host memory, written by the device.
+struct ServeCompletion {
+  unsigned long long seq;  // ticket + 1 once the request is complete
+  unsigned long long t_first_ns, t_done_ns;  // device global timer
+  int status;
+  int pad;
+};
+
+// Host-written control block in mapped host memory.
+struct ServeCtrl {
+  unsigned long long class_tail[8];  // requests published per class
+  int stop;
+  int pad[3];
+};
+
+struct ServeArgs {
+  ServeSlot* slots;             // device, one per ring slot
+  const int* class_ring;        // mapped host: [class][cap] slot of the k-th request
+  const ServeCtrl* ctrl;        // mapped host
+  ServeCompletion* comp;        // mapped host, one per ring slot
+  unsigned long long* class_head;  // device: first request of the class with work left
+  int cls, cap;
+  int PB, PR, PEX;
+  unsigned long long idle_ns;   // exit after this long without work
+};
+
+template <class T>
+__device__ __forceinline__ T volatile_load(const T* p) {
+  return *const_cast<const volatile T*>(p);
+}
+
+// Thread 0 finds an unclaimed instance of the oldest request of its class.
+// Waits are bounded: it returns -1 on the stop flag or after idle_ns of
+// global time without work.
+__device__ __forceinline__ void claim_next(const ServeArgs& s, int64_t* slot) {
+  if (threadIdx.x != 0) return;
+  const uint64_t t0 = global_timer_ns();
+  while (true) {
+    if (volatile_load(&s.ctrl->stop)) {
+      *slot = -1;
+      return;
+    }
+    const unsigned long long head = volatile_load(&s.class_head[s.cls]);
+    const unsigned long long tail = volatile_load(&s.ctrl->class_tail[s.cls]);
+    if (head < tail) {
+      const int sl = volatile_load(&s.class_ring[s.cls * s.cap + int(head % s.cap)]);
+      ServeSlot* rs = s.slots + sl;
+      const unsigned long long inst = atomicAdd(&rs->claim, 1ull);
+      if (inst < static_cast<unsigned long long>(rs->d.n_inst)) {
+        if (inst == 0) s.comp[sl].t_first_ns = global_timer_ns();
+        *slot = (int64_t(sl) << 32) | int64_t(inst);
+        return;
+      }
+      atomicCAS(&s.class_head[s.cls], head, head + 1);  // request fully handed out
+      continue;
+    }
+    if (global_timer_ns() - t0 > s.idle_ns) {
+      *slot = -1;
+      return;
+    }
+    __nanosleep(256);
+  }
+}
+
+// Non-blocking form: -2 when no work is available yet (try again later).
+__device__ __forceinline__ void claim_try(const ServeArgs& s, int64_t* slot) {
+  if (threadIdx.x != 0) return;
+  while (true) {
+    if (volatile_load(&s.ctrl->stop)) {
+      *slot = -1;
+      return;
+    }
+    const unsigned long long head = volatile_load(&s.class_head[s.cls]);
+    const unsigned long long tail = volatile_load(&s.ctrl->class_tail[s.cls]);
+    if (head >= tail) {
+      *slot = -2;
+      return;
+    }
+    const int sl = volatile_load(&s.class_ring[s.cls * s.cap + int(head % s.cap)]);
+    ServeSlot* rs = s.slots + sl;
+    const unsigned long long inst = atomicAdd(&rs->claim, 1ull);
+    if (inst < static_cast<unsigned long long>(rs->d.n_inst)) {
+      if (inst == 0) s.comp[sl].t_first_ns = global_timer_ns();
+      *slot = (int64_t(sl) << 32) | int64_t(inst);
+      return;
+    }
+    atomicCAS(&s.class_head[s.cls], head, head + 1);
+  }
+}
+
+// Thread 0, after an instance's outputs and status are stored: counts it and,
+// for the request's last instance, publishes the completion to the host.
+__device__ __forceinline__ void serve_done(const ServeArgs& s, int64_t w, int status) {
+  const int sl = int(w >> 32);
+  ServeSlot* rs = s.slots + sl;
+  if (status) atomicOr(&rs->status, status);
+  __threadfence_system();
+  const unsigned long long prev = atomicAdd(&rs->done, 1ull);
+  if (prev + 1 == static_cast<unsigned long long>(rs->d.n_inst)) {
+    __threadfence_system();
+    ServeCompletion* c = s.comp + sl;
+    c->status = volatile_load(&rs->status);
+    c->t_done_ns = global_timer_ns();
+    __threadfence_system();
+    *const_cast<volatile unsigned long long*>(&c->seq) = rs->ticket + 1;
+  }
+}
+
+__device__ __forceinline__ DetItem det_item(const ServeArgs& s, int64_t w) {
+  BatchArgs b{};
+  const int sl = int(w >> 32);
+  const int2 wu = make_int2(0, int(w & 0xffffffff));
+  b.desc = &s.slots[sl].d;
+  b.work = &wu;
+  return det_item(b, 0);
+}
+
+__device__ __forceinline__ PreItem pre_item(const ServeArgs& s, int64_t w) {
+  BatchArgs b{};
+  const int sl = int(w >> 32);
+  const int2 wu = make_int2(0, int(w & 0xffffffff));
+  b.desc = &s.slots[sl].d;
+  b.work = &wu;
+  return pre_item(b, 0);
+}
+
 // Claims the next work unit of a batch: thread 0 bumps the counter and
 // publishes the index in shared memory; readers wait for the next barrier.
 __device__ __forceinline__ void claim_next(const BatchArgs& b, int64_t* slot) {
@@ -299,6 +440,9 @@ __device__ __forceinline__ void claim_next(const BatchArgs& b, int64_t* slot) {
     const unsigned long long w = atomicAdd(b.counter, 1ull);
     *slot = w < static_cast<unsigned long long>(b.n_work) ? static_cast<int64_t>(w) : -1;
   }
+}
+__device__ __forceinline__ void claim_try(const BatchArgs& b, int64_t* slot) {
+  claim_next(b, slot);
 }
 
 // ---------------------------------------------------------------------------
@@ -867,10 +1011,19 @@ template <class S> struct SrcTraits;
 template <> struct SrcTraits<DetectArgs> { static constexpr bool kDyn = false; };
 template <> struct SrcTraits<PrecodeArgs> { static constexpr bool kDyn = false; };
 template <> struct SrcTraits<BatchArgs> { static constexpr bool kDyn = true; };
+template <> struct SrcTraits<ServeArgs> { static constexpr bool kDyn = true; };
+
+// Per-instance completion hook (serving only).
+template <class S>
+__device__ __forceinline__ void src_done(const S&, int64_t, int) {}
+__device__ __forceinline__ void src_done(const ServeArgs& s, int64_t w, int status) {
+  serve_done(s, w, status);
+}
 
 __device__ __forceinline__ int64_t src_count(const DetectArgs& a) { return a.n_inst; }
 __device__ __forceinline__ int64_t src_count(const PrecodeArgs& a) { return a.n_inst; }
 __device__ __forceinline__ int64_t src_count(const BatchArgs& b) { return b.n_work; }
+__device__ __forceinline__ int64_t src_count(const ServeArgs&) { return 0; }
 
 template <int UT, int EL, bool X3, bool FULL, class Src>
 __device__ __forceinline__ void detect_tc_body(const Src& src, int PB, int PU, int PR,
@@ -961,7 +1114,7 @@ __device__ __forceinline__ void detect_tc_body(const Src& src, int PB, int PU, i
     __syncthreads();
     tc_reduce_warp<UT, EL, NT>(part, WK, U, R, it.sigma, sA, sAc, sBm, sGd);
     tc_zero_padding<UT>(U, R, sA, sAc, sBm, sGd, NTHR);
-    if constexpr (kDyn) claim_next(src, sClaim);
+    if constexpr (kDyn) claim_try(src, sClaim);  // never blocks the current instance
     __syncthreads();
     int64_t next;
     if constexpr (kDyn) {
@@ -970,7 +1123,7 @@ __device__ __forceinline__ void detect_tc_body(const Src& src, int PB, int PU, i
       next = cur + gridDim.x < count ? cur + gridDim.x : -1;
     }
     DetItem nit{};
-    if (next >= 0) nit = det_item(src, next);
+    if (next >= 0) nit = det_item(src, next);  // -1: no more work; -2: ask again later
     if (next >= 0 && nit.bulk && !it.exact && tid == 0) {
       fence_proxy_async_smem();
       issue(nit);
@@ -1033,7 +1186,25 @@ __device__ __forceinline__ void detect_tc_body(const Src& src, int PB, int PU, i
       write_detect_outputs<UT, NTHR>(o, 0, sX, sMu, sRho, sStatus);
     }
     __syncthreads();
-    if (tid == 0 && it.status) *it.status = *sStatus;
+    if (tid == 0) {
+      const int st = *sStatus;
+      if (it.status) *it.status = st;
+      src_done(src, cur, st);
+    }
+    if constexpr (kDyn) {
+      if (next == -2) {  // nothing was ready earlier: wait for work now (bounded)
+        claim_next(src, sClaim);
+        __syncthreads();
+        next = *sClaim;
+        if (next >= 0) {
+          nit = det_item(src, next);
+          if (nit.bulk && tid == 0) {
+            fence_proxy_async_smem();
+            issue(nit);
+          }
+        }
+      }
+    }
     cur = next;
     it = nit;
   }
@@ -1286,9 +1457,14 @@ __device__ __forceinline__ void precode_tc_body(const Src& src, int PB, int PU, 
         }
       }
     }
+    __syncthreads();
+    if (tid == 0) {
+      const int st = *sStatus;
+      if (a.status) *a.status = st;
+      src_done(src, n, st);
+    }
     if constexpr (kDyn) claim_next(src, sClaim);
     __syncthreads();
-    if (tid == 0 && a.status) *a.status = *sStatus;
     if constexpr (kDyn) {
       n = *sClaim;
     } else {
@@ -1307,6 +1483,20 @@ template <int UT, int EL, bool X3, bool FULL>
 __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
     precode_tc_batch_kernel(const BatchArgs b) {
   precode_tc_body<UT, EL, X3, FULL>(b, b.PB, UT, b.PR);
+}
+
+// Serving kernels: one per (operation, padded user count); every CTA claims
+// instances of the oldest request of its class until stopped or idle.
+template <int UT, int EL, bool X3>
+__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
+    detect_tc_serve_kernel(const ServeArgs s) {
+  detect_tc_body<UT, EL, X3, false>(s, s.PB, UT, s.PR, s.PEX);
+}
+
+template <int UT, int EL, bool X3>
+__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
+    precode_tc_serve_kernel(const ServeArgs s) {
+  precode_tc_body<UT, EL, X3, false>(s, s.PB, UT, s.PR);
 }
 
 }  // namespace cgm

@@ -38,6 +38,11 @@ cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const Ba
                             int max_grid, cudaStream_t s, bool launch, uint32_t* smem_out,
                             int* grid_out);
 
+// Serving kernels (tc.cu): one persistent kernel per (operation, UT). With
+// launch = false only the shared-memory size and resident CTAs are computed.
+cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
+                            cudaStream_t st, bool launch, uint32_t* smem_out, int* resident_out);
+
 // Dynamic shared memory of one CTA for the given shape (bytes).
 uint32_t detect_smem_bytes(int UT, int B, int U, int R, int exact);
 uint32_t precode_smem_bytes(int UT, int B, int U, int R);

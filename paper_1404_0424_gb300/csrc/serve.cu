@@ -1,0 +1,327 @@
+// Host side of the serving loop behind cg_serve_*: ring slots, admission by
+// HBM budget, publication through mapped host memory, on-demand launch of
+// the persistent class kernels, completion polling and bounded shutdown.
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <ctime>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "cgmimo.h"
+#include "host_checks.h"
+#include "launch.cuh"
+
+using namespace cgm;
+
+namespace {
+
+constexpr int kClasses = 6;  // (detect, precode) x (UT 8, 16, 32)
+
+int64_t mono_ns() {
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return int64_t(ts.tv_sec) * 1000000000LL + ts.tv_nsec;
+}
+
+int class_of(const cg_desc& d, int* UT) {
+  const int pu = padded_users(d.U);
+  *UT = pu < 8 ? 8 : pu;
+  return d.op * 3 + (*UT == 8 ? 0 : *UT == 16 ? 1 : 2);
+}
+
+int64_t footprint(const cg_desc& d) {
+  const int64_t n = d.n_inst, B = d.B, U = d.U, R = d.R, q = d.qam_bits;
+  if (d.op == CG_OP_DETECT) return n * ((B * U + R * B) * 8 + R * U * (16 + 4 * q) + 4);
+  return n * ((B * U + R * U) * 8 + R * B * 8 + R * 4 + 4);
+}
+
+struct SlotInfo {
+  uint64_t ticket = ~0ull;
+  int cls = 0;
+  int64_t bytes = 0;
+  int64_t submit_ns = 0;
+  int64_t complete_ns = 0;
+  bool released = true;
+};
+
+}  // namespace
+
+struct cg_server {
+  int dev = 0;
+  cg_serve_cfg cfg{};
+  int el = 1;
+  bool x3 = true;
+  void* dmem = nullptr;
+  ServeSlot* d_slots = nullptr;
+  unsigned long long* d_head = nullptr;
+  void* hmem = nullptr;
+  int* h_ring = nullptr;
+  ServeCtrl* h_ctrl = nullptr;
+  ServeCompletion* h_comp = nullptr;
+  int* d_ring = nullptr;
+  ServeCtrl* d_ctrl = nullptr;
+  ServeCompletion* d_comp = nullptr;
+  cudaStream_t ks[kClasses] = {};
+  cudaStream_t cs = nullptr;
+  bool launched[kClasses] = {};
+  int grid[kClasses] = {};
+  std::mutex mu;
+  uint64_t next = 0, head = 0;
+  uint64_t published[kClasses] = {};
+  std::vector<SlotInfo> info;
+  int64_t inflight = 0;
+};
+
+namespace {
+
+ServeArgs args_for(const cg_server* s, int cls) {
+  ServeArgs a{};
+  a.slots = s->d_slots;
+  a.class_ring = s->d_ring;
+  a.ctrl = s->d_ctrl;
+  a.comp = s->d_comp;
+  a.class_head = s->d_head;
+  a.cls = cls;
+  a.cap = s->cfg.capacity;
+  a.PB = s->cfg.max_B;
+  a.PR = s->cfg.max_R;
+  a.PEX = cls < 3 ? 1 : 0;
+  a.idle_ns = (unsigned long long)s->cfg.idle_timeout_ms * 1000000ull;
+  return a;
+}
+
+int class_ut(int cls) { return cls % 3 == 0 ? 8 : cls % 3 == 1 ? 16 : 32; }
+
+// Launches the class kernel if it is not running (never launched, or its
+// previous launch has exited on the idle timeout).
+int ensure_running(cg_server* s, int cls) {
+  if (s->launched[cls]) {
+    const cudaError_t q = cudaStreamQuery(s->ks[cls]);
+    if (q == cudaErrorNotReady) return CG_OK;
+    if (q != cudaSuccess) return CG_ECUDA;
+  }
+  const cudaError_t err = launch_serve_tc(cls / 3, class_ut(cls), s->el, s->x3, args_for(s, cls),
+                                          s->grid[cls], s->ks[cls], true, nullptr, nullptr);
+  if (err != cudaSuccess) return CG_ECUDA;
+  s->launched[cls] = true;
+  return CG_OK;
+}
+
+bool complete(const cg_server* s, uint64_t ticket) {
+  const ServeCompletion* c = s->h_comp + ticket % uint64_t(s->cfg.capacity);
+  const auto* seq = reinterpret_cast<const std::atomic<unsigned long long>*>(&c->seq);
+  return seq->load(std::memory_order_acquire) == ticket + 1;
+}
+
+// Retires finished requests from the head of the ring and releases their bytes.
+void retire(cg_server* s) {
+  while (s->head < s->next) {
+    SlotInfo& in = s->info[s->head % uint64_t(s->cfg.capacity)];
+    if (!complete(s, s->head)) break;
+    if (!in.released) {
+      s->inflight -= in.bytes;
+      in.released = true;
+    }
+    ++s->head;
+  }
+}
+
+void destroy_server(cg_server* s) {
+  for (int c = 0; c < kClasses; ++c)
+    if (s->ks[c]) cudaStreamDestroy(s->ks[c]);
+  if (s->cs) cudaStreamDestroy(s->cs);
+  if (s->dmem) cudaFree(s->dmem);
+  if (s->hmem) cudaFreeHost(s->hmem);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
+  if (cfg == nullptr || out == nullptr) return CG_EINVAL;
+  *out = nullptr;
+  const cg_serve_cfg c = *cfg;
+  if (c.capacity < 1 || c.capacity > (1 << 20)) return CG_EINVAL;
+  if (c.precision < CG_PREC_BF16 || c.precision > CG_PREC_FP16X3) return CG_EINVAL;
+  if (c.hbm_budget_bytes <= 0) return CG_EINVAL;
+  if (c.max_B < 1 || c.max_B > CG_B_MAX || c.max_R < 1 || c.max_R > CG_R_MAX) return CG_EINVAL;
+  if (c.ctas_per_class < 0 || c.idle_timeout_ms < 1 || c.idle_timeout_ms > 60000)
+    return CG_EINVAL;
+  cg_server* s = new cg_server();
+  s->cfg = c;
+  s->el = (c.precision == CG_PREC_BF16 || c.precision == CG_PREC_BF16X3) ? 0 : 1;
+  s->x3 = c.precision == CG_PREC_BF16X3 || c.precision == CG_PREC_FP16X3;
+  s->info.resize(size_t(c.capacity));
+  if (cudaGetDevice(&s->dev) != cudaSuccess) {
+    delete s;
+    return CG_ECUDA;
+  }
+  const size_t cap = size_t(c.capacity);
+  const size_t dbytes = sizeof(ServeSlot) * cap + sizeof(unsigned long long) * 8;
+  const size_t ring_bytes = (sizeof(int) * kClasses * cap + 255) & ~size_t(255);
+  const size_t ctrl_off = ring_bytes;
+  const size_t comp_off = (ctrl_off + sizeof(ServeCtrl) + 255) & ~size_t(255);
+  const size_t hbytes = comp_off + sizeof(ServeCompletion) * cap;
+  int rc = CG_OK;
+  if (cudaMalloc(&s->dmem, dbytes) != cudaSuccess) {
+    s->dmem = nullptr;
+    rc = CG_ENOMEM;
+  }
+  if (rc == CG_OK && cudaHostAlloc(&s->hmem, hbytes, cudaHostAllocMapped) != cudaSuccess) {
+    s->hmem = nullptr;
+    rc = CG_ENOMEM;
+  }
+  if (rc == CG_OK) {
+    std::memset(s->hmem, 0, hbytes);
+    s->d_slots = static_cast<ServeSlot*>(s->dmem);
+    s->d_head = reinterpret_cast<unsigned long long*>(s->d_slots + cap);
+    char* h = static_cast<char*>(s->hmem);
+    s->h_ring = reinterpret_cast<int*>(h);
+    s->h_ctrl = reinterpret_cast<ServeCtrl*>(h + ctrl_off);
+    s->h_comp = reinterpret_cast<ServeCompletion*>(h + comp_off);
+    void* dv = nullptr;
+    if (cudaHostGetDevicePointer(&dv, s->hmem, 0) != cudaSuccess) rc = CG_ECUDA;
+    char* d = static_cast<char*>(dv);
+    s->d_ring = reinterpret_cast<int*>(d);
+    s->d_ctrl = reinterpret_cast<ServeCtrl*>(d + ctrl_off);
+    s->d_comp = reinterpret_cast<ServeCompletion*>(d + comp_off);
+  }
+  if (rc == CG_OK && cudaMemset(s->dmem, 0, dbytes) != cudaSuccess) rc = CG_ECUDA;
+  for (int k = 0; k < kClasses && rc == CG_OK; ++k)
+    if (cudaStreamCreateWithFlags(&s->ks[k], cudaStreamNonBlocking) != cudaSuccess) rc = CG_ECUDA;
+  if (rc == CG_OK && cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess)
+    rc = CG_ECUDA;
+  // launch shapes: an equal share of each class kernel's resident CTAs
+  DeviceInfo di;
+  if (rc == CG_OK && device_info(&di) != 0) rc = CG_ECUDA;
+  for (int k = 0; k < kClasses && rc == CG_OK; ++k) {
+    uint32_t smem = 0;
+    int resident = 0;
+    const cudaError_t err = launch_serve_tc(k / 3, class_ut(k), s->el, s->x3, args_for(s, k), 0,
+                                            nullptr, false, &smem, &resident);
+    if (err != cudaSuccess) {
+      rc = err == cudaErrorInvalidValue ? CG_EINVAL : CG_ECUDA;
+      break;
+    }
+    const int share = resident / kClasses;
+    s->grid[k] = c.ctas_per_class > 0 ? c.ctas_per_class : (share > 0 ? share : 1);
+  }
+  if (rc != CG_OK) {
+    destroy_server(s);
+    return rc;
+  }
+  *out = s;
+  return CG_OK;
+}
+
+int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket) {
+  if (s == nullptr || req == nullptr || ticket == nullptr) return CG_EINVAL;
+  const cg_desc d = *req;
+  cg_params p{};
+  p.B = d.B;
+  p.U = d.U;
+  p.qam_bits = d.qam_bits;
+  p.K = d.K;
+  p.R = d.R;
+  p.N0 = d.N0;
+  p.Es = d.Es;
+  p.sinr_mode = d.sinr_mode;
+  p.amul_mode = CG_AMUL_EXPLICIT;
+  p.precision = s->cfg.precision;
+  if (d.n_inst < 1 || d.B > s->cfg.max_B || d.R > s->cfg.max_R) return CG_EINVAL;
+  int rc;
+  if (d.op == CG_OP_DETECT)
+    rc = check_detect(&p, d.n_inst, d.H, d.in, d.out, d.mu, d.rho, d.aux, d.status);
+  else if (d.op == CG_OP_PRECODE)
+    rc = check_precode(&p, d.n_inst, d.H, d.in, d.out, d.aux, d.status);
+  else
+    rc = CG_EINVAL;
+  if (rc != CG_OK) return rc;
+  const int64_t bytes = footprint(d);
+  if (bytes > s->cfg.hbm_budget_bytes) return CG_ETOOBIG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != s->dev) return CG_EINVAL;
+  retire(s);
+  const uint64_t cap = uint64_t(s->cfg.capacity);
+  if (s->next - s->head >= cap) return CG_EAGAIN;
+  if (s->inflight + bytes > s->cfg.hbm_budget_bytes) return CG_EAGAIN;
+  int UT;
+  const int cls = class_of(d, &UT);
+  const uint64_t t = s->next;
+  const uint64_t slot = t % cap;
+  ServeSlot rec{};
+  rec.d = d;
+  rec.ticket = t;
+  std::memset(&s->h_comp[slot], 0, sizeof(ServeCompletion));
+  if (cudaMemcpyAsync(s->d_slots + slot, &rec, sizeof(rec), cudaMemcpyHostToDevice, s->cs) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s->cs) != cudaSuccess)
+    return CG_ECUDA;
+  s->h_ring[cls * s->cfg.capacity + int(s->published[cls] % cap)] = int(slot);
+  ++s->published[cls];
+  reinterpret_cast<std::atomic<unsigned long long>*>(&s->h_ctrl->class_tail[cls])
+      ->store(s->published[cls], std::memory_order_release);
+  SlotInfo& in = s->info[slot];
+  in.ticket = t;
+  in.cls = cls;
+  in.bytes = bytes;
+  in.submit_ns = mono_ns();
+  in.complete_ns = 0;
+  in.released = false;
+  s->inflight += bytes;
+  s->next = t + 1;
+  *ticket = t;
+  return ensure_running(s, cls);
+}
+
+int cg_serve_poll(cg_server* s, uint64_t ticket, int32_t* done, cg_req_stats* stats) {
+  if (s == nullptr || done == nullptr) return CG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  const uint64_t cap = uint64_t(s->cfg.capacity);
+  SlotInfo& in = s->info[ticket % cap];
+  if (ticket >= s->next || in.ticket != ticket) return CG_EINVAL;
+  *done = complete(s, ticket) ? 1 : 0;
+  if (*done) {
+    if (in.complete_ns == 0) in.complete_ns = mono_ns();
+    if (stats) {
+      const ServeCompletion* c = s->h_comp + ticket % cap;
+      stats->status = c->status;
+      stats->pad = 0;
+      stats->submit_ns = in.submit_ns;
+      stats->complete_ns = in.complete_ns;
+      stats->device_first_ns = int64_t(c->t_first_ns);
+      stats->device_done_ns = int64_t(c->t_done_ns);
+    }
+    retire(s);
+    return CG_OK;
+  }
+  // not done: make sure its class kernel is alive (it may have idled out just
+  // before the request was published)
+  return ensure_running(s, in.cls);
+}
+
+int cg_serve_destroy(cg_server* s) {
+  if (s == nullptr) return CG_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    reinterpret_cast<std::atomic<int>*>(&s->h_ctrl->stop)->store(1, std::memory_order_release);
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int k = 0; k < kClasses; ++k) {
+    while (s->launched[k]) {
+      const cudaError_t q = cudaStreamQuery(s->ks[k]);
+      if (q != cudaErrorNotReady) break;
+      if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(10)) return CG_ETIMEDOUT;
+      std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+  }
+  destroy_server(s);
+  return CG_OK;
+}
+
+}  // extern "C"

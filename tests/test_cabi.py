@@ -102,3 +102,15 @@ def test_plan_rejects_invalid_descriptors_on_the_host(lib):
     assert cabi.cg_plan_create([good], 9)[0] == cabi.CG_EINVAL
     assert lib.cg_plan_run(None, None) == cabi.CG_EINVAL
     assert lib.cg_plan_destroy(None) == cabi.CG_EINVAL
+
+
+def test_serve_rejects_invalid_configuration_on_the_host(lib):
+    for bad in (dict(capacity=0), dict(precision=0), dict(precision=7), dict(hbm_budget_bytes=0),
+                dict(max_B=0), dict(max_B=257), dict(max_R=17), dict(ctas_per_class=-1),
+                dict(idle_timeout_ms=0), dict(idle_timeout_ms=120000)):
+        rc, srv = cabi.cg_serve_create(**bad)
+        assert rc == cabi.CG_EINVAL and srv is None, bad
+    good = cabi.CgDesc(0, 32, 4, 1, 3, 4, 0, 0, 0.5, 1.0, 1, 16, 16, 16, None, None, None, None)
+    assert cabi.cg_serve_submit(None, good)[0] == cabi.CG_EINVAL
+    assert cabi.cg_serve_poll(None, 0)[0] == cabi.CG_EINVAL
+    assert lib.cg_serve_destroy(None) == cabi.CG_EINVAL
