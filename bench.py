@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--precision", default="fp16x3", choices=list(PRECISIONS))
     ap.add_argument("--no-plain", action="store_true", help="skip timing the FP32 plain path")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     return ap.parse_args()
 
 
@@ -176,6 +179,93 @@ def time_oracle(seconds: float, Un: int, K: int):
     dt = time.perf_counter() - t0
     _ = np
     return solves / dt, inst, dt
+
+
+# ---------------------------------------------------------------------------
+# uneven batch (4096 problems) and serving (Poisson arrivals)
+# ---------------------------------------------------------------------------
+
+def run_batched(cabi, torch, dev, n_prob=4096, seed=2, reps=10):
+    """4096 detection problems, (B, U) uniform over {64x8, 128x16, 128x32,
+    256x32}, 16/64/256-QAM, 1-14 symbols, SNR uniform 5-25 dB, K = min(U/4, 8),
+    one instance each; one plan (CG_PREC_AUTO), one graph launch per run."""
+    import numpy as np
+    from paper_1404_0424_gb300 import workload as wl
+    rng = np.random.default_rng(seed)
+    shapes = [(64, 8), (128, 16), (128, 32), (256, 32)]
+    keep, descs, solves, nbytes = [], [], 0, 0
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    for _ in range(n_prob):
+        B, U = shapes[rng.integers(4)]
+        R = int(rng.integers(1, 15))
+        q = int(rng.choice([4, 6, 8]))
+        K = max(1, min(U // 4, 8))
+        N0 = wl.snr_to_n0(float(rng.uniform(5, 25)), U)
+        H = torch.randn((1, B, U), dtype=torch.complex64, device=dev, generator=g)
+        Y = torch.randn((1, R, B), dtype=torch.complex64, device=dev, generator=g)
+        o = [torch.empty((1, R, U), dtype=torch.complex64, device=dev),
+             torch.empty((1, R, U), device=dev), torch.empty((1, R, U), device=dev),
+             torch.empty((1, R, U, q), device=dev), torch.empty((1,), dtype=torch.int32,
+                                                                device=dev)]
+        keep.append((H, Y, o, B, U, R, K, q, N0))
+        descs.append(cabi.desc(0, B, U, R, K, N0, H, Y, o[0], qam_bits=q, mu=o[1], rho=o[2],
+                               aux=o[3], status=o[4]))
+        solves += R
+        nbytes += detect_bytes_per_instance(B, U, R, q)
+    stream = torch.cuda.current_stream(dev)
+    rc, plan, bad = cabi.cg_plan_create(descs, -1, stream)
+    if rc:
+        return {"error": cabi.cg_strerror(rc)}
+    _, prec, nbins = cabi.cg_plan_info(plan)
+    for _ in range(3):
+        cabi.cg_plan_run(plan, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        cabi.cg_plan_run(plan, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    cabi.cg_plan_destroy(plan)
+    # one FP32 launch per problem (the plain form of the same batch)
+    e0.record(stream)
+    for H, Y, o, B, U, R, K, q, N0 in keep:
+        p = cabi.params(B, U, q, K, R, N0, precision=0)
+        cabi.cg_detect(p, 1, H, Y, o[0], o[1], o[2], o[3], o[4], stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    ok = all(int(o[4][0]) == 0 for _, _, o, *_ in keep)
+    return {"workload": "4096 uneven detection problems: (B,U) in {64x8,128x16,128x32,256x32}, "
+                        "16/64/256-QAM, 1-14 symbols, SNR 5-25 dB, K=min(U/4,8)",
+            "precision": {3: "bf16x3", 4: "fp16x3"}.get(prec, prec), "bins": nbins,
+            "ms_per_run": round(ms, 4), "solves_per_s": round(solves / (ms / 1e3), 1),
+            "gb_per_s": round(nbytes / (ms / 1e3) / 1e9, 1),
+            "plain_one_launch_per_problem": {"ms": round(ms_plain, 3),
+                                             "solves_per_s": round(solves / (ms_plain / 1e3), 1)},
+            "status_ok": ok}
+
+
+def run_serving(seconds):
+    """Poisson arrivals at 20k requests/s (the load generator's mix), served
+    (cg_serve_*, FP16X3) and plain (one FP32 launch per request)."""
+    from paper_1404_0424_gb300 import build as bld
+    out = {}
+    for mode in ("served", "plain"):
+        cmd = [bld.LOADGEN, "--mode", mode, "--rate", "20000", "--seconds", str(seconds),
+               "--capacity", "64", "--precision", "4", "--seed", "1"]
+        try:
+            res = subprocess.run(cmd, capture_output=True, text=True, timeout=seconds + 120)
+            line = res.stdout.strip().splitlines()[-1] if res.stdout.strip() else "{}"
+            out[mode] = json.loads(line)
+        except Exception as exc:  # noqa: BLE001
+            out[mode] = {"error": repr(exc)}
+    out["workload"] = ("Poisson 20k req/s, 50/50 detect/precode, B in {64,128,256}, "
+                       "U in {8,16,32}, 16/64/256-QAM, 12-1200 subcarriers, 1-14 symbols, "
+                       "SNR 5-25 dB, K=min(U/4,8); latency from scheduled arrival")
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -347,6 +437,13 @@ def run_ours(args):
     pre_bytes = precode_bytes_per_instance(B, Un, R) * n
     pre_gbs = pre_bytes / (pre_ms / 1e3) / 1e9
 
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = run_batched(cabi, torch, dev)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serving = run_serving(args.serve_seconds)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, ninst, dt = time_oracle(args.cpu_seconds, Un, K)
@@ -374,10 +471,15 @@ def run_ours(args):
             "precode_solves_per_s": round(n * R * world / (pre_ms / 1e3), 1),
             "detect_ms": round(det_ms, 4), "precode_ms": round(pre_ms, 4),
             "precode_gbs": round(pre_gbs, 1),
-            "latency_ms": {"plain_slot_p50": round(lat[len(lat) // 2], 4),
-                           "plain_slot_p99": round(lat[min(len(lat) - 1,
-                                                           int(0.99 * len(lat)))], 4),
-                           "what": "one 1200x14 slot, detect + precode, one launch each"},
+            "latency_ms": {"slot_p50": round(lat[len(lat) // 2], 4),
+                           "slot_p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4),
+                           "slot_what": "one 1200x14 slot, detect + precode, one launch each",
+                           "served_p50": (serving or {}).get("served", {}).get("lat_p50_ms"),
+                           "served_p99": (serving or {}).get("served", {}).get("lat_p99_ms"),
+                           "plain_p50": (serving or {}).get("plain", {}).get("lat_p50_ms"),
+                           "plain_p99": (serving or {}).get("plain", {}).get("lat_p99_ms")},
+            "batched": batched,
+            "serving": serving,
             "roofline": roofline,
             "plain_fp32": plain,
             "cpu_baseline": cpu,

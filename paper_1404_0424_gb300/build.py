@@ -19,6 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libcgmimo.so")
+LOADGEN_SRC = os.path.join(PKG, "loadgen", "serve_load.cu")
+LOADGEN = os.path.join(BUILD, "cgmimo_serve_load")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
@@ -38,13 +40,14 @@ def _sources():
 
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
+        glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h")) + \
+        [os.path.abspath(__file__), LOADGEN_SRC]
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(LOADGEN):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LOADGEN))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -77,6 +80,12 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
     os.replace(tmp, LIB)
+    # the serving load generator links the library it sits next to
+    cmd = [cc, *ARCH, "-O2", "-std=c++17", "-I" + INCLUDE, LOADGEN_SRC, "-o", LOADGEN,
+           "-L" + BUILD, "-lcgmimo", "-Xlinker", "-rpath,$ORIGIN", "-cudart", "shared"]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"load generator build failed:\n{res.stdout}\n{res.stderr}")
     return LIB
 
 
