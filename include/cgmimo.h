@@ -235,17 +235,21 @@ typedef struct cg_server cg_server;
  * their work overlaps on the device. Every device wait is bounded. */
 int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out);
 
-/* Non-blocking submit of one request (a cg_desc with n_inst >= 1 whose
- * DEVICE buffers stay valid until it completes). Returns CG_EAGAIN when all
- * ring slots are in use or admitting it would exceed the HBM budget (poll
+/* Non-blocking submit of one request (a cg_desc with 1 <= n_inst < 2^24
+ * whose DEVICE buffers stay valid until it completes). Returns CG_EAGAIN when
+ * all ring slots are in use or admitting it would exceed the HBM budget (poll
  * and retry), CG_EINVAL for an invalid request, CG_ETOOBIG when it alone
- * exceeds the budget; on success *ticket identifies it. */
+ * exceeds the budget or has 2^24 instances or more; on success *ticket
+ * identifies it. A request's bytes count against the budget until it
+ * completes; its ring slot stays in use until a cg_serve_poll has reported
+ * it done, so poll every ticket until done. Slots are freed in ticket order. */
 int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket);
 
 /* *done = 1 once every instance of the request is finished and its outputs
- * are visible to the host; stats (may be NULL) are filled when done. Poll a
- * ticket before `capacity` newer requests are submitted (its slot is then
- * reused and the call returns CG_EINVAL). */
+ * are visible to the host; stats (may be NULL) are filled when done. The
+ * first poll that reports done releases the ticket's slot; later polls of
+ * the same ticket report done again until the slot is reused by a newer
+ * request, after which they return CG_EINVAL. */
 int cg_serve_poll(cg_server* s, uint64_t ticket, int32_t* done, cg_req_stats* stats);
 
 /* Stops the class kernels (bounded wait) and frees the server. Requests still

@@ -296,16 +296,22 @@ __device__ __forceinline__ PreItem pre_item(const BatchArgs& b, int64_t w) {
 // Serving: requests published by the host, claimed instance by instance
 // ---------------------------------------------------------------------------
 
-// Device copy of one request (written by the host at submit) and its
-// progress counters.
+// Device copy of one request (written by the host at submit, before the
+// request is published) and its progress counters.
 struct ServeSlot {
   cg_desc d;
-  unsigned long long claim;   // next instance to hand out
+  unsigned long long claim;   // (ticket & 0xffffffff) << 32 | next instance to hand out
   unsigned long long done;    // instances finished
   unsigned long long ticket;  // submit ticket of the request in this slot
   int status;                 // OR of the instances' status words
   int pad;
 };
+
+// A published request in a class ring: ticket << 24 | instance count. The
+// count travels with the ticket, so a claim never depends on a descriptor
+// that the host may be rewriting for a later request in the same slot.
+constexpr int SERVE_NINST_BITS = 24;
+constexpr unsigned long long SERVE_NINST_MASK = (1ull << SERVE_NINST_BITS) - 1ull;
 
 // Completion record in mapped host memory, written by the device.
 struct ServeCompletion {
@@ -324,7 +330,7 @@ struct ServeCtrl {
 
 struct ServeArgs {
   ServeSlot* slots;             // device, one per ring slot
-  const int* class_ring;        // mapped host: [class][cap] slot of the k-th request
+  const unsigned long long* class_ring;  // mapped host: [class][cap] published entries
   const ServeCtrl* ctrl;        // mapped host
   ServeCompletion* comp;        // mapped host, one per ring slot
   unsigned long long* class_head;  // device: first request of the class with work left
@@ -336,6 +342,33 @@ struct ServeArgs {
 template <class T>
 __device__ __forceinline__ T volatile_load(const T* p) {
   return *const_cast<const volatile T*>(p);
+}
+
+// One claim attempt on the request at the class head. Returns the claimed
+// work unit (slot << 32 | instance), or -1 when that request has nothing
+// left to hand out (the head is then advanced past it). The claim word
+// carries the request's ticket, so a stale view of the ring or of the head
+// can neither claim an instance of a later request that reuses the slot
+// nor claim past the request's instance count.
+__device__ __forceinline__ int64_t serve_claim_at(const ServeArgs& s, unsigned long long head) {
+  const unsigned long long e = volatile_load(&s.class_ring[s.cls * s.cap + int(head % s.cap)]);
+  const unsigned long long ticket = e >> SERVE_NINST_BITS;
+  const unsigned long long n = e & SERVE_NINST_MASK;
+  const int sl = int(ticket % unsigned(s.cap));
+  ServeSlot* rs = s.slots + sl;
+  const unsigned long long tag = (ticket & 0xffffffffull) << 32;
+  unsigned long long w = volatile_load(&rs->claim);
+  while ((w & 0xffffffff00000000ull) == tag && (w & 0xffffffffull) < n) {
+    const unsigned long long prev = atomicCAS(&rs->claim, w, w + 1ull);
+    if (prev == w) {
+      const unsigned long long inst = w & 0xffffffffull;
+      if (inst == 0) s.comp[sl].t_first_ns = global_timer_ns();
+      return (int64_t(sl) << 32) | int64_t(inst);
+    }
+    w = prev;
+  }
+  atomicCAS(&s.class_head[s.cls], head, head + 1ull);  // request fully handed out
+  return -1;
 }
 
 // Thread 0 finds an unclaimed instance of the oldest request of its class.
@@ -352,15 +385,11 @@ __device__ __forceinline__ void claim_next(const ServeArgs& s, int64_t* slot) {
     const unsigned long long head = volatile_load(&s.class_head[s.cls]);
     const unsigned long long tail = volatile_load(&s.ctrl->class_tail[s.cls]);
     if (head < tail) {
-      const int sl = volatile_load(&s.class_ring[s.cls * s.cap + int(head % s.cap)]);
-      ServeSlot* rs = s.slots + sl;
-      const unsigned long long inst = atomicAdd(&rs->claim, 1ull);
-      if (inst < static_cast<unsigned long long>(rs->d.n_inst)) {
-        if (inst == 0) s.comp[sl].t_first_ns = global_timer_ns();
-        *slot = (int64_t(sl) << 32) | int64_t(inst);
+      const int64_t w = serve_claim_at(s, head);
+      if (w >= 0) {
+        *slot = w;
         return;
       }
-      atomicCAS(&s.class_head[s.cls], head, head + 1);  // request fully handed out
       continue;
     }
     if (global_timer_ns() - t0 > s.idle_ns) {
@@ -385,16 +414,24 @@ __device__ __forceinline__ void claim_try(const ServeArgs& s, int64_t* slot) {
       *slot = -2;
       return;
     }
-    const int sl = volatile_load(&s.class_ring[s.cls * s.cap + int(head % s.cap)]);
-    ServeSlot* rs = s.slots + sl;
-    const unsigned long long inst = atomicAdd(&rs->claim, 1ull);
-    if (inst < static_cast<unsigned long long>(rs->d.n_inst)) {
-      if (inst == 0) s.comp[sl].t_first_ns = global_timer_ns();
-      *slot = (int64_t(sl) << 32) | int64_t(inst);
+    const int64_t w = serve_claim_at(s, head);
+    if (w >= 0) {
+      *slot = w;
       return;
     }
-    atomicCAS(&s.class_head[s.cls], head, head + 1);
   }
+}
+
+// Copy of a slot's descriptor read at L2 (bypassing L1, which may still hold
+// the descriptor of an earlier request in the same slot).
+__device__ __forceinline__ cg_desc serve_desc(const ServeSlot* rs) {
+  static_assert(sizeof(cg_desc) % 8 == 0, "descriptor is copied in 8-byte words");
+  cg_desc d;
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&rs->d);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&d);
+#pragma unroll
+  for (int k = 0; k < int(sizeof(cg_desc) / 8); ++k) dst[k] = __ldcg(src + k);
+  return d;
 }
 
 // Thread 0, after an instance's outputs and status are stored: counts it and,
@@ -404,31 +441,32 @@ __device__ __forceinline__ void serve_done(const ServeArgs& s, int64_t w, int st
   ServeSlot* rs = s.slots + sl;
   if (status) atomicOr(&rs->status, status);
   __threadfence_system();
+  const unsigned long long n = static_cast<unsigned long long>(__ldcg(&rs->d.n_inst));
   const unsigned long long prev = atomicAdd(&rs->done, 1ull);
-  if (prev + 1 == static_cast<unsigned long long>(rs->d.n_inst)) {
+  if (prev + 1 == n) {
     __threadfence_system();
     ServeCompletion* c = s.comp + sl;
-    c->status = volatile_load(&rs->status);
+    c->status = atomicOr(&rs->status, 0);
     c->t_done_ns = global_timer_ns();
     __threadfence_system();
-    *const_cast<volatile unsigned long long*>(&c->seq) = rs->ticket + 1;
+    *const_cast<volatile unsigned long long*>(&c->seq) = __ldcg(&rs->ticket) + 1;
   }
 }
 
 __device__ __forceinline__ DetItem det_item(const ServeArgs& s, int64_t w) {
-  BatchArgs b{};
-  const int sl = int(w >> 32);
+  const cg_desc d = serve_desc(s.slots + int(w >> 32));
   const int2 wu = make_int2(0, int(w & 0xffffffff));
-  b.desc = &s.slots[sl].d;
+  BatchArgs b{};
+  b.desc = &d;
   b.work = &wu;
   return det_item(b, 0);
 }
 
 __device__ __forceinline__ PreItem pre_item(const ServeArgs& s, int64_t w) {
-  BatchArgs b{};
-  const int sl = int(w >> 32);
+  const cg_desc d = serve_desc(s.slots + int(w >> 32));
   const int2 wu = make_int2(0, int(w & 0xffffffff));
-  b.desc = &s.slots[sl].d;
+  BatchArgs b{};
+  b.desc = &d;
   b.work = &wu;
   return pre_item(b, 0);
 }

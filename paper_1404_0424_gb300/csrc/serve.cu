@@ -43,7 +43,8 @@ struct SlotInfo {
   int64_t bytes = 0;
   int64_t submit_ns = 0;
   int64_t complete_ns = 0;
-  bool released = true;
+  bool released = true;  // its bytes no longer count against the budget
+  bool reaped = true;    // a poll has reported it done: the slot may be reused
 };
 
 }  // namespace
@@ -57,10 +58,10 @@ struct cg_server {
   ServeSlot* d_slots = nullptr;
   unsigned long long* d_head = nullptr;
   void* hmem = nullptr;
-  int* h_ring = nullptr;
+  unsigned long long* h_ring = nullptr;
   ServeCtrl* h_ctrl = nullptr;
   ServeCompletion* h_comp = nullptr;
-  int* d_ring = nullptr;
+  unsigned long long* d_ring = nullptr;
   ServeCtrl* d_ctrl = nullptr;
   ServeCompletion* d_comp = nullptr;
   cudaStream_t ks[kClasses] = {};
@@ -115,17 +116,18 @@ bool complete(const cg_server* s, uint64_t ticket) {
   return seq->load(std::memory_order_acquire) == ticket + 1;
 }
 
-// Retires finished requests from the head of the ring and releases their bytes.
+// Releases the budget bytes of every completed request, then frees the
+// ring slots at the head whose requests a poll has reported done.
 void retire(cg_server* s) {
-  while (s->head < s->next) {
-    SlotInfo& in = s->info[s->head % uint64_t(s->cfg.capacity)];
-    if (!complete(s, s->head)) break;
-    if (!in.released) {
+  const uint64_t cap = uint64_t(s->cfg.capacity);
+  for (uint64_t t = s->head; t < s->next; ++t) {
+    SlotInfo& in = s->info[t % cap];
+    if (!in.released && complete(s, t)) {
       s->inflight -= in.bytes;
       in.released = true;
     }
-    ++s->head;
   }
+  while (s->head < s->next && s->info[s->head % cap].reaped) ++s->head;
 }
 
 void destroy_server(cg_server* s) {
@@ -162,7 +164,7 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
   }
   const size_t cap = size_t(c.capacity);
   const size_t dbytes = sizeof(ServeSlot) * cap + sizeof(unsigned long long) * 8;
-  const size_t ring_bytes = (sizeof(int) * kClasses * cap + 255) & ~size_t(255);
+  const size_t ring_bytes = (sizeof(unsigned long long) * kClasses * cap + 255) & ~size_t(255);
   const size_t ctrl_off = ring_bytes;
   const size_t comp_off = (ctrl_off + sizeof(ServeCtrl) + 255) & ~size_t(255);
   const size_t hbytes = comp_off + sizeof(ServeCompletion) * cap;
@@ -180,13 +182,13 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
     s->d_slots = static_cast<ServeSlot*>(s->dmem);
     s->d_head = reinterpret_cast<unsigned long long*>(s->d_slots + cap);
     char* h = static_cast<char*>(s->hmem);
-    s->h_ring = reinterpret_cast<int*>(h);
+    s->h_ring = reinterpret_cast<unsigned long long*>(h);
     s->h_ctrl = reinterpret_cast<ServeCtrl*>(h + ctrl_off);
     s->h_comp = reinterpret_cast<ServeCompletion*>(h + comp_off);
     void* dv = nullptr;
     if (cudaHostGetDevicePointer(&dv, s->hmem, 0) != cudaSuccess) rc = CG_ECUDA;
     char* d = static_cast<char*>(dv);
-    s->d_ring = reinterpret_cast<int*>(d);
+    s->d_ring = reinterpret_cast<unsigned long long*>(d);
     s->d_ctrl = reinterpret_cast<ServeCtrl*>(d + ctrl_off);
     s->d_comp = reinterpret_cast<ServeCompletion*>(d + comp_off);
   }
@@ -243,6 +245,7 @@ int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket) {
   if (rc != CG_OK) return rc;
   const int64_t bytes = footprint(d);
   if (bytes > s->cfg.hbm_budget_bytes) return CG_ETOOBIG;
+  if (uint64_t(d.n_inst) > SERVE_NINST_MASK) return CG_ETOOBIG;
   std::lock_guard<std::mutex> lk(s->mu);
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != s->dev) return CG_EINVAL;
@@ -254,15 +257,19 @@ int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket) {
   const int cls = class_of(d, &UT);
   const uint64_t t = s->next;
   const uint64_t slot = t % cap;
+  if (t >> (64 - SERVE_NINST_BITS)) return CG_ETOOBIG;  // ticket space exhausted
   ServeSlot rec{};
   rec.d = d;
   rec.ticket = t;
+  rec.claim = (t & 0xffffffffull) << 32;
   std::memset(&s->h_comp[slot], 0, sizeof(ServeCompletion));
   if (cudaMemcpyAsync(s->d_slots + slot, &rec, sizeof(rec), cudaMemcpyHostToDevice, s->cs) !=
           cudaSuccess ||
       cudaStreamSynchronize(s->cs) != cudaSuccess)
     return CG_ECUDA;
-  s->h_ring[cls * s->cfg.capacity + int(s->published[cls] % cap)] = int(slot);
+  reinterpret_cast<std::atomic<unsigned long long>*>(
+      &s->h_ring[cls * s->cfg.capacity + int(s->published[cls] % cap)])
+      ->store((t << SERVE_NINST_BITS) | uint64_t(d.n_inst), std::memory_order_relaxed);
   ++s->published[cls];
   reinterpret_cast<std::atomic<unsigned long long>*>(&s->h_ctrl->class_tail[cls])
       ->store(s->published[cls], std::memory_order_release);
@@ -273,6 +280,7 @@ int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket) {
   in.submit_ns = mono_ns();
   in.complete_ns = 0;
   in.released = false;
+  in.reaped = false;
   s->inflight += bytes;
   s->next = t + 1;
   *ticket = t;
@@ -288,6 +296,7 @@ int cg_serve_poll(cg_server* s, uint64_t ticket, int32_t* done, cg_req_stats* st
   *done = complete(s, ticket) ? 1 : 0;
   if (*done) {
     if (in.complete_ns == 0) in.complete_ns = mono_ns();
+    in.reaped = true;
     if (stats) {
       const ServeCompletion* c = s->h_comp + ticket % cap;
       stats->status = c->status;

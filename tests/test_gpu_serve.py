@@ -199,3 +199,57 @@ def test_idle_exit_relaunch_and_shutdown_in_flight(cabi):
     finally:
         assert cabi.cg_serve_destroy(srv) == 0   # stops with work possibly in flight
     torch.cuda.synchronize()
+
+
+def test_slots_are_reused_only_after_poll_and_results_hold_under_reuse(cabi):
+    """Many more requests than ring slots, of every class: a finished request
+    keeps its slot until polled (submit says CG_EAGAIN meanwhile), a poll
+    never fails for a ticket still in flight, and every result equals the
+    single-shape call although each slot is reused many times."""
+    dev = torch.device("cuda:0")
+    reqs = make_requests(dev, n_req=60, seed=21)
+    for r in reqs:                          # keep each request small: frequent reuse
+        r["n"] = min(r["n"], 40)
+        r["H"] = r["H"][:r["n"]].contiguous()
+        r["inp"] = r["inp"][:r["n"]].contiguous()
+    outs = [fresh_outputs(r, dev) for r in reqs]
+    rc, srv = cabi.cg_serve_create(capacity=4, precision=4, idle_timeout_ms=300)
+    assert rc == 0, cabi.cg_strerror(rc)
+    try:
+        # fill every slot, let the requests finish unpolled: no slot frees up
+        first = [submit(cabi, srv, as_desc(cabi, r, o)) for r, o in zip(reqs[:4], outs[:4])]
+        torch.cuda.synchronize()   # returns once the class kernels have idled out
+        assert all(bool((outs[k]["status"] == 0).all()) for k in range(4))
+        assert cabi.cg_serve_submit(srv, as_desc(cabi, reqs[4], outs[4]))[0] == cabi.CG_EAGAIN
+        wait_done(cabi, srv, first)
+        # a reaped ticket reports done again while its slot is not reused
+        rc, done, _ = cabi.cg_serve_poll(srv, first[0])
+        assert rc == 0 and done == 1
+        # the rest, polled lazily as in a load generator
+        pending, k = {}, 4
+        t0 = time.monotonic()
+        while k < len(reqs) or pending:
+            while k < len(reqs):
+                rc, t = cabi.cg_serve_submit(srv, as_desc(cabi, reqs[k], outs[k]))
+                if rc == cabi.CG_EAGAIN:
+                    break
+                assert rc == 0, cabi.cg_strerror(rc)
+                pending[t] = k
+                k += 1
+            for t in list(pending):
+                rc, done, st = cabi.cg_serve_poll(srv, t)
+                assert rc == 0, f"poll of in-flight ticket {t}: {cabi.cg_strerror(rc)}"
+                if done:
+                    assert st.status == 0
+                    del pending[t]
+            assert time.monotonic() - t0 < 60, "requests did not finish"
+    finally:
+        assert cabi.cg_serve_destroy(srv) == 0
+    for r, m in zip(reqs, outs):
+        if r["op"] == 0:
+            ref = cabi.detect(r["H"], r["inp"], r["N0"], r["K"], r["q"], precision=4)
+        else:
+            ref = cabi.precode(r["H"], r["inp"], r["N0"], r["K"], precision=4)
+        torch.cuda.synchronize()
+        for key in m:
+            assert torch.equal(m[key], ref[key]), f"served {key} differs from the single call"
