@@ -293,7 +293,7 @@ def run_ours(args):
     import numpy as np
     import torch
 
-    from paper_1404_0424_gb300 import build, cabi, workload as wl
+    from paper_1404_0424_gb300 import build, cabi, shard, workload as wl
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -359,10 +359,7 @@ def run_ours(args):
     elapsed_ms = t_start.elapsed_time(t_end)
     det_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     pre_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = shard.max_over_ranks(elapsed_ms, dist, dev)   # timing only
 
     ms_step = elapsed_ms / args.steps
     solves_step = 2 * n * R * world
