@@ -81,7 +81,11 @@ int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void*
     int el;
     bool x3;
     tc_mode(p->precision, &el, &x3);
-    err = launch_detect_tc(padded_users(p->U), el, x3, a, s, nullptr);
+    const int UT = padded_users(p->U);
+    if (UT <= 16 && !a.exact)
+      err = launch_detect_warp(UT, el, x3, a, s);
+    else
+      err = launch_detect_tc(UT, el, x3, a, s, nullptr);
   }
   if (err == cudaErrorInvalidValue) return CG_EINVAL;
   return err == cudaSuccess ? CG_OK : CG_ECUDA;
@@ -111,7 +115,11 @@ int precode_device(const cg_params* p, int64_t n_inst, const void* H, const void
     int el;
     bool x3;
     tc_mode(p->precision, &el, &x3);
-    err = launch_precode_tc(padded_users(p->U), el, x3, a, s, nullptr);
+    const int UT = padded_users(p->U);
+    if (UT <= 16)
+      err = launch_precode_warp(UT, el, x3, a, s);
+    else
+      err = launch_precode_tc(UT, el, x3, a, s, nullptr);
   }
   if (err == cudaErrorInvalidValue) return CG_EINVAL;
   return err == cudaSuccess ? CG_OK : CG_ECUDA;

@@ -371,33 +371,29 @@ __device__ __forceinline__ int64_t serve_claim_at(const ServeArgs& s, unsigned l
   return -1;
 }
 
-// Thread 0 finds an unclaimed instance of the oldest request of its class.
-// Waits are bounded: it returns -1 on the stop flag or after idle_ns of
+// One thread finds an unclaimed instance of the oldest request of its class
+// and returns it. Waits are bounded: -1 on the stop flag or after idle_ns of
 // global time without work.
-__device__ __forceinline__ void claim_next(const ServeArgs& s, int64_t* slot) {
-  if (threadIdx.x != 0) return;
+__device__ __forceinline__ int64_t serve_claim_wait(const ServeArgs& s) {
   const uint64_t t0 = global_timer_ns();
   while (true) {
-    if (volatile_load(&s.ctrl->stop)) {
-      *slot = -1;
-      return;
-    }
+    if (volatile_load(&s.ctrl->stop)) return -1;
     const unsigned long long head = volatile_load(&s.class_head[s.cls]);
     const unsigned long long tail = volatile_load(&s.ctrl->class_tail[s.cls]);
     if (head < tail) {
       const int64_t w = serve_claim_at(s, head);
-      if (w >= 0) {
-        *slot = w;
-        return;
-      }
+      if (w >= 0) return w;
       continue;
     }
-    if (global_timer_ns() - t0 > s.idle_ns) {
-      *slot = -1;
-      return;
-    }
+    if (global_timer_ns() - t0 > s.idle_ns) return -1;
     __nanosleep(256);
   }
+}
+
+// Thread 0 claims for its CTA (serve_claim_wait) into shared memory.
+__device__ __forceinline__ void claim_next(const ServeArgs& s, int64_t* slot) {
+  if (threadIdx.x != 0) return;
+  *slot = serve_claim_wait(s);
 }
 
 // Non-blocking form: -2 when no work is available yet (try again later).

@@ -1,0 +1,850 @@
+// Warp-per-instance tensor-core kernels for CG-D and CG-P with up to 16 users.
+//
+// One warp owns one instance (a channel H with its R <= 16 right-hand sides)
+// from its first load to its last store, so no CTA barrier is involved:
+//   1. H and Y (or T) are read straight from global memory into m16n8k16
+//      fragments with coalesced 16-byte loads, one k-step of 8 antennas
+//      ahead of the products that consume it;
+//   2. G = H^H H and the transposed matched filters B^T = Y^T conj(H)
+//      (Algorithm 1 line 5) accumulate on the tensor cores;
+//   3. Algorithm 1 lines 7-16 run entirely in registers. Users are numbered
+//      in a "position" order chosen so that the Gram accumulators of a lane
+//      are exactly its B fragments of e = A p, and the matched-filter
+//      accumulators are exactly the layout of the CG vectors: accumulator
+//      row = right-hand side, accumulator column = position. Inner products
+//      over users are quad shuffles (compensated sums);
+//   4. x_hat, mu, rho and the max-log LLRs of Eq. 4 (CG-D) or q = H v (CG-P,
+//      Algorithm 1 line 20) are stored from the registers that hold them.
+//
+// Position P (0 <= P < 8 NB) holds user pos_user(P); with 16 users the two
+// 8-blocks interleave (P = 8 nt + w holds user 2 w + nt), which makes the
+// users a lane touches contiguous in memory. Every product is a split
+// (hi + lo) one in X3 mode, as in cg_tc.cuh; e = A p always is.
+#pragma once
+
+#include "cg_tc.cuh"
+
+#ifndef CGM_WARP_MINB
+#define CGM_WARP_MINB 4  // resident CTAs per SM the register allocation targets
+#endif
+
+namespace cgm {
+
+template <int UT>
+struct WarpCfg {
+  static_assert(UT == 8 || UT == 16, "warp kernels serve 8 or 16 padded users");
+  static constexpr int NB = UT / 8;     // 8-position blocks
+  static constexpr int NFRAG = NB * NB * 2 * 2;  // CG B fragments: (ks, nt, b0/b1, re/im)
+  static constexpr int WARPS = 4;       // warps per CTA (independent)
+  static constexpr int NTHR = 32 * WARPS;
+  // per warp: the CG B fragments (one uint2 per lane and fragment), then
+  // alpha_k, beta_k of the 16 right-hand-side rows for the tracker
+  static constexpr uint32_t FRAG_BYTES = uint32_t(NFRAG) * 32u * 8u;
+  static constexpr uint32_t AB_BYTES = uint32_t(KMAX) * 16u * 2u * 4u;
+  static constexpr uint32_t WARP_BYTES = FRAG_BYTES + AB_BYTES;
+  static constexpr uint32_t SMEM = uint32_t(WARPS) * WARP_BYTES;
+};
+
+template <int UT>
+__host__ __device__ constexpr int pos_user(int P) {
+  return UT == 16 ? 2 * (P & 7) + (P >> 3) : P;
+}
+
+__device__ __forceinline__ float4 ldg4(const float2* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float2 ldg2(const float2* p) { return __ldg(p); }
+
+// Compensated butterfly over the four lanes of a quad (lane bits 0 and 1)
+// for two independent sums.
+__device__ __forceinline__ void quad_sum2(float& x0, float& x1) {
+  float s0 = x0, s1 = x1, c0 = 0.f, c1 = 0.f;
+#pragma unroll
+  for (int off = 1; off < 4; off <<= 1) {
+    const float so0 = __shfl_xor_sync(0xffffffffu, s0, off);
+    const float so1 = __shfl_xor_sync(0xffffffffu, s1, off);
+    const float co0 = __shfl_xor_sync(0xffffffffu, c0, off);
+    const float co1 = __shfl_xor_sync(0xffffffffu, c1, off);
+    const float t0 = s0 + so0, t1 = s1 + so1;
+    const float b0 = t0 - s0, b1 = t1 - s1;
+    const float e0 = (s0 - (t0 - b0)) + (so0 - b0);
+    const float e1 = (s1 - (t1 - b1)) + (so1 - b1);
+    s0 = t0;
+    s1 = t1;
+    c0 = (c0 + co0) + e0;
+    c1 = (c1 + co1) + e1;
+  }
+  x0 = s0 + c0;
+  x1 = s1 + c1;
+}
+
+// ---------------------------------------------------------------------------
+// Loads of one k-step (antennas b0 = 8 ks + 2 t and b0 + 1)
+// ---------------------------------------------------------------------------
+
+// h[0..3]: H(b0, row user 0), H(b0, row user 1), H(b0+1, row user 0),
+// H(b0+1, row user 1); the row users of lane g are 2g, 2g+1 (16) or g (8).
+// VEC: U == UT, B even, H 16-byte aligned.
+template <int UT, bool VEC>
+__device__ __forceinline__ void load_h_ks(const float2* __restrict__ H, int B, int U, int ks,
+                                          int g, int t, float2 (&h)[4]) {
+  const int b0 = 8 * ks + 2 * t, b1 = b0 + 1;
+  const float2 z = make_float2(0.f, 0.f);
+  if constexpr (VEC) {
+    const bool ok = b0 < B;
+    if constexpr (UT == 16) {
+      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v0 = ok ? ldg4(H + b0 * 16 + 2 * g) : zero4;
+      const float4 v1 = ok ? ldg4(H + b1 * 16 + 2 * g) : zero4;
+      h[0] = make_float2(v0.x, v0.y);
+      h[1] = make_float2(v0.z, v0.w);
+      h[2] = make_float2(v1.x, v1.y);
+      h[3] = make_float2(v1.z, v1.w);
+    } else {
+      h[0] = ok ? ldg2(H + b0 * 8 + g) : z;
+      h[2] = ok ? ldg2(H + b1 * 8 + g) : z;
+      h[1] = h[3] = z;
+    }
+  } else {
+    const int u0 = UT == 16 ? 2 * g : g, u1 = 2 * g + 1;
+    h[0] = (b0 < B && u0 < U) ? ldg2(H + b0 * U + u0) : z;
+    h[2] = (b1 < B && u0 < U) ? ldg2(H + b1 * U + u0) : z;
+    if constexpr (UT == 16) {
+      h[1] = (b0 < B && u1 < U) ? ldg2(H + b0 * U + u1) : z;
+      h[3] = (b1 < B && u1 < U) ? ldg2(H + b1 * U + u1) : z;
+    } else {
+      h[1] = h[3] = z;
+    }
+  }
+}
+
+// y[0..3]: Y(g, b0), Y(g+8, b0), Y(g, b0+1), Y(g+8, b0+1) (rows >= R are 0).
+// VEC: B even, Y 16-byte aligned.
+template <bool VEC>
+__device__ __forceinline__ void load_y_ks(const float2* __restrict__ Y, int B, int R, int ks,
+                                          int g, int t, float2 (&y)[4]) {
+  const int b0 = 8 * ks + 2 * t, b1 = b0 + 1;
+  const float2 z = make_float2(0.f, 0.f);
+  if constexpr (VEC) {
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool ok = b0 < B;
+    const float4 w0 = (ok && g < R) ? ldg4(Y + g * B + b0) : zero4;
+    const float4 w1 = (ok && g + 8 < R) ? ldg4(Y + (g + 8) * B + b0) : zero4;
+    y[0] = make_float2(w0.x, w0.y);
+    y[2] = make_float2(w0.z, w0.w);
+    y[1] = make_float2(w1.x, w1.y);
+    y[3] = make_float2(w1.z, w1.w);
+  } else {
+    y[0] = (g < R && b0 < B) ? ldg2(Y + g * B + b0) : z;
+    y[2] = (g < R && b1 < B) ? ldg2(Y + g * B + b1) : z;
+    y[1] = (g + 8 < R && b0 < B) ? ldg2(Y + (g + 8) * B + b0) : z;
+    y[3] = (g + 8 < R && b1 < B) ? ldg2(Y + (g + 8) * B + b1) : z;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gram (and transposed matched filters) of one k-step
+// ---------------------------------------------------------------------------
+
+// Gr/Gi[nt][d]: G at row position 8 (d >> 1) + g, column position
+// 8 nt + 2 t + (d & 1). Mr[nt][d] = Re b^T and Mn[nt][d] = -Im b^T at
+// right-hand side g + 8 (d >> 1), column position 8 nt + 2 t + (d & 1).
+template <int UT, int EL, bool X3, bool MF>
+__device__ __forceinline__ void gram_ks(const float2 (&h)[4], const float2 (&y)[4],
+                                        float (&Gr)[UT / 8][4], float (&Gi)[UT / 8][4],
+                                        float (&Mr)[UT / 8][4], float (&Mn)[UT / 8][4]) {
+  constexpr int NB = UT / 8;
+  uint2 hs[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) hs[k] = split_c<EL>(h[k]);
+  const uint32_t ah[4] = {hs[0].x, hs[1].x, hs[2].x, hs[3].x};
+  const uint32_t al[4] = {hs[0].y, hs[1].y, hs[2].y, hs[3].y};
+  uint32_t yh[4], yl[4];
+  if constexpr (MF) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint2 s = split_c<EL>(y[k]);
+      yh[k] = s.x;
+      yl[k] = s.y;
+    }
+  }
+#pragma unroll
+  for (int nt = 0; nt < NB; ++nt) {
+    // B fragments of n-tile nt: the row-user registers of block nt
+    const uint2 b0 = hs[nt], b1 = hs[2 + nt];
+    const uint32_t s0h = swap_neg(b0.x), s1h = swap_neg(b1.x);
+    const uint32_t s0l = swap_neg(b0.y), s1l = swap_neg(b1.y);
+    mma_split<EL, X3>(Gr[nt], ah, al, b0.x, b1.x, b0.y, b1.y);
+    mma_split<EL, X3>(Gi[nt], ah, al, s0h, s1h, s0l, s1l);
+    if constexpr (MF) {
+      mma_split<EL, X3>(Mr[nt], yh, yl, b0.x, b1.x, b0.y, b1.y);
+      mma_split<EL, X3>(Mn[nt], yh, yl, s0h, s1h, s0l, s1l);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 in registers
+// ---------------------------------------------------------------------------
+
+// CG state of one warp: entry [h][nt][c] is right-hand side g + 8 h at
+// position 8 nt + 2 t + c. The B fragments of A (plain and times i, hi|lo)
+// live in this warp's shared-memory slice, one uint2 per lane and fragment.
+template <int UT, int EL>
+struct WarpCg {
+  static constexpr int NB = UT / 8;
+  float2 v[2][NB][2], res[2][NB][2], p[2][NB][2];
+  float D[NB][2];
+  float rrn[2];
+  bool active[2], broke[2];
+  int kd[2];  // iterations completed per row
+
+  // Fragment index of (ks, nt, b, part) in the shared slice.
+  __device__ __forceinline__ static int fidx(int ks, int nt, int b, int part) {
+    return ((ks * NB + nt) * 2 + b) * 2 + part;
+  }
+
+  // Writes A = G + sigma I as B fragments (from the Gram accumulators) and
+  // returns D = diag(A) and G_ii at the lane's positions.
+  __device__ __forceinline__ static void setup_a(const float (&Gr)[NB][4], const float (&Gi)[NB][4],
+                                                 float sigma, uint2* frag, float (&Dout)[NB][2],
+                                                 float (&Gd)[NB][2]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int ks = 0; ks < NB; ++ks)
+#pragma unroll
+      for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          // A[8 ks + 2 t + b][8 nt + g] = conj(G[8 nt + g][8 ks + 2 t + b]) (+ sigma)
+          const int d = 2 * nt + b;
+          const bool diag = (ks == nt) && (g == 2 * t + b);
+          const float re = Gr[ks][d] + (diag ? sigma : 0.f);
+          const float im = diag ? 0.f : -Gi[ks][d];
+          frag[fidx(ks, nt, b, 0) * 32 + lane] = split_c<EL>(make_float2(re, im));
+          frag[fidx(ks, nt, b, 1) * 32 + lane] = split_c<EL>(make_float2(-im, re));
+        }
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float gd = __shfl_sync(0xffffffffu, Gr[nt][2 * nt + c], 4 * (2 * t + c) + t);
+        Gd[nt][c] = gd;
+        Dout[nt][c] = gd + sigma;
+      }
+  }
+
+  // e = A p for every right-hand side row: E[nt][d] in accumulator layout.
+  __device__ __forceinline__ void matvec(const uint2* frag, float (&Er)[NB][4],
+                                         float (&Ei)[NB][4]) const {
+    const int lane = threadIdx.x & 31;
+    uint32_t ph[NB][4], pl[NB][4];
+#pragma unroll
+    for (int ks = 0; ks < NB; ++ks) {
+      const uint2 s0 = split_c<EL>(p[0][ks][0]);  // row g, q = t
+      const uint2 s1 = split_c<EL>(p[1][ks][0]);  // row g + 8, q = t
+      const uint2 s2 = split_c<EL>(p[0][ks][1]);  // row g, q = t + 4
+      const uint2 s3 = split_c<EL>(p[1][ks][1]);  // row g + 8, q = t + 4
+      ph[ks][0] = s0.x; pl[ks][0] = s0.y;
+      ph[ks][1] = s1.x; pl[ks][1] = s1.y;
+      ph[ks][2] = s2.x; pl[ks][2] = s2.y;
+      ph[ks][3] = s3.x; pl[ks][3] = s3.y;
+    }
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt) {
+      float rh[4] = {0.f, 0.f, 0.f, 0.f}, rx[4] = {0.f, 0.f, 0.f, 0.f};
+      float ih[4] = {0.f, 0.f, 0.f, 0.f}, ix[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ks = 0; ks < NB; ++ks) {
+        const uint2 r0 = frag[fidx(ks, nt, 0, 0) * 32 + lane];
+        const uint2 r1 = frag[fidx(ks, nt, 1, 0) * 32 + lane];
+        const uint2 i0 = frag[fidx(ks, nt, 0, 1) * 32 + lane];
+        const uint2 i1 = frag[fidx(ks, nt, 1, 1) * 32 + lane];
+        mma16816<EL>(rh, ph[ks], r0.x, r1.x);
+        mma16816<EL>(ih, ph[ks], i0.x, i1.x);
+        mma16816<EL>(rx, ph[ks], r0.y, r1.y);
+        mma16816<EL>(ix, ph[ks], i0.y, i1.y);
+        mma16816<EL>(rx, pl[ks], r0.x, r1.x);
+        mma16816<EL>(ix, pl[ks], i0.x, i1.x);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Er[nt][k] = rh[k] + rx[k];
+        Ei[nt][k] = ih[k] + ix[k];
+      }
+    }
+  }
+
+  // Lines 7-14 of Algorithm 1. res holds b on entry; rows >= R are
+  // inactive from the start. With TRACK, alpha_k and beta_k of every row are
+  // kept in sAB[(k - 1) * 16 + row] for the tracker (tracker_l below).
+  template <bool TRACK>
+  __device__ __forceinline__ void run(const uint2* frag, float2* sAB, int R, int K) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float s[2] = {0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          v[h][nt][c] = make_float2(0.f, 0.f);
+          p[h][nt][c] = res[h][nt][c];
+          s[h] = fmaf(res[h][nt][c].x, res[h][nt][c].x,
+                      fmaf(res[h][nt][c].y, res[h][nt][c].y, s[h]));
+        }
+    quad_sum2(s[0], s[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      rrn[h] = s[h];
+      active[h] = (g + 8 * h) < R;
+      broke[h] = false;
+      kd[h] = 0;
+    }
+    for (int k = 1; k <= K; ++k) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (active[h] && !(rrn[h] > 0.f)) {
+          active[h] = false;
+          broke[h] = true;
+        }
+      if (!__any_sync(0xffffffffu, active[0] || active[1])) break;
+      float Er[NB][4], Ei[NB][4];
+      matvec(frag, Er, Ei);
+      float pe[2] = {0.f, 0.f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const float2 pp = p[h][nt][c];
+            pe[h] = fmaf(pp.x, Er[nt][2 * h + c], fmaf(pp.y, Ei[nt][2 * h + c], pe[h]));
+          }
+      quad_sum2(pe[0], pe[1]);
+      float alpha[2], rrnew[2] = {0.f, 0.f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (active[h] && !(pe[h] > 0.f)) {
+          active[h] = false;
+          broke[h] = true;
+        }
+        alpha[h] = active[h] ? __fdividef(rrn[h], pe[h]) : 0.f;
+#pragma unroll
+        for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (active[h]) {
+              v[h][nt][c].x = fmaf(alpha[h], p[h][nt][c].x, v[h][nt][c].x);
+              v[h][nt][c].y = fmaf(alpha[h], p[h][nt][c].y, v[h][nt][c].y);
+              res[h][nt][c].x = fmaf(-alpha[h], Er[nt][2 * h + c], res[h][nt][c].x);
+              res[h][nt][c].y = fmaf(-alpha[h], Ei[nt][2 * h + c], res[h][nt][c].y);
+            }
+            rrnew[h] = fmaf(res[h][nt][c].x, res[h][nt][c].x,
+                            fmaf(res[h][nt][c].y, res[h][nt][c].y, rrnew[h]));
+          }
+      }
+      quad_sum2(rrnew[0], rrnew[1]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!active[h]) continue;
+        const float beta = __fdividef(rrnew[h], rrn[h]);
+#pragma unroll
+        for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            p[h][nt][c].x = fmaf(beta, p[h][nt][c].x, res[h][nt][c].x);
+            p[h][nt][c].y = fmaf(beta, p[h][nt][c].y, res[h][nt][c].y);
+          }
+        if (TRACK && t == 0) sAB[(k - 1) * 16 + g + 8 * h] = make_float2(alpha[h], beta);
+        rrn[h] = rrnew[h];
+        kd[h] = k;
+      }
+    }
+  }
+
+  // Eq. 11 with A replaced by D (scalar per position) from the recorded
+  // alpha_k, beta_k: l_1 = alpha_1, and for k >= 2
+  //   l_k = l_{k-1} + (alpha_k (1 + beta_{k-1}) / alpha_{k-1} - alpha_k D)(l_{k-1} - l_{k-2})
+  //         - alpha_k beta_{k-2} / alpha_{k-2} (l_{k-2} - l_{k-3}),
+  // with alpha = 1, beta = 0, l = 0 before the first iteration. Returns
+  // l_{kd} of row h at the lane's positions (0 when no iteration completed).
+  __device__ __forceinline__ void tracker_l(const float2* sAB, int h, float (&l)[NB][2]) const {
+    const int g = (threadIdx.x & 31) >> 2;
+    const int row = g + 8 * h;
+    float l1[NB][2], l2[NB][2], l3[NB][2];
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) l1[nt][c] = l2[nt][c] = l3[nt][c] = 0.f;
+    float ia1 = 1.f, ia2 = 1.f, be1 = 0.f, be2 = 0.f;
+    for (int k = 1; k <= kd[h]; ++k) {
+      const float2 ab = sAB[(k - 1) * 16 + row];
+      const float al = ab.x;
+      const float c1 = al * (1.f + be1) * ia1;
+      const float c2 = al * be2 * ia2;
+#pragma unroll
+      for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float lk = (k == 1) ? al
+                                    : l1[nt][c] + (c1 - al * D[nt][c]) * (l1[nt][c] - l2[nt][c]) -
+                                          c2 * (l2[nt][c] - l3[nt][c]);
+          l3[nt][c] = l2[nt][c];
+          l2[nt][c] = l1[nt][c];
+          l1[nt][c] = lk;
+        }
+      ia2 = ia1;
+      ia1 = __fdividef(1.f, al);
+      be2 = be1;
+      be1 = ab.y;
+    }
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) l[nt][c] = l1[nt][c];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Work sources at warp granularity
+// ---------------------------------------------------------------------------
+
+// Lane 0 claims, every lane gets the unit (-1: none).
+__device__ __forceinline__ int64_t warp_claim(const BatchArgs& b) {
+  int64_t w = -1;
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned long long u = atomicAdd(b.counter, 1ull);
+    w = u < static_cast<unsigned long long>(b.n_work) ? static_cast<int64_t>(u) : -1;
+  }
+  return __shfl_sync(0xffffffffu, w, 0);
+}
+
+__device__ __forceinline__ int64_t warp_claim(const ServeArgs& s) {
+  int64_t w = -1;
+  if ((threadIdx.x & 31) == 0) w = serve_claim_wait(s);
+  return __shfl_sync(0xffffffffu, w, 0);
+}
+
+template <class S>
+__device__ __forceinline__ int64_t warp_first(const S& s, int64_t gw) {
+  if constexpr (SrcTraits<S>::kDyn) {
+    return warp_claim(s);
+  } else {
+    return gw < src_count(s) ? gw : -1;
+  }
+}
+
+template <class S>
+__device__ __forceinline__ int64_t warp_next(const S& s, int64_t cur, int64_t nw) {
+  if constexpr (SrcTraits<S>::kDyn) {
+    return warp_claim(s);
+  } else {
+    return cur + nw < src_count(s) ? cur + nw : -1;
+  }
+}
+
+__device__ __forceinline__ bool al16(const void* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// Stores of one lane's detection outputs
+// ---------------------------------------------------------------------------
+
+// The 2 NB users of a lane in one right-hand-side row, in memory order
+// (16 users: 4t + m holds position (nt, c) = (m & 1, m >> 1); 8 users:
+// 2t + m holds (0, m)). VEC: contiguous users, 16-byte aligned rows.
+template <int UT, int QB, bool VEC>
+__device__ __forceinline__ void store_row_detect(const DetItem& it, int r, int t,
+                                                 const float2 (&x)[UT / 8][2],
+                                                 const float (&mu)[UT / 8][2],
+                                                 const float (&rho)[UT / 8][2], float cq,
+                                                 int* flags) {
+  constexpr int NB = UT / 8, NU = 2 * NB, H = QB / 2;
+  const int u0 = UT == 16 ? 4 * t : 2 * t;
+  const int64_t base = int64_t(r) * it.U + u0;
+  float2 xo[NU];
+  float mo[NU], ro[NU];
+#pragma unroll
+  for (int m = 0; m < NU; ++m) {
+    const int nt = UT == 16 ? (m & 1) : 0, c = UT == 16 ? (m >> 1) : m;
+    xo[m] = x[nt][c];
+    mo[m] = mu[nt][c];
+    ro[m] = rho[nt][c];
+  }
+  if constexpr (VEC) {
+    if (it.xhat) {
+      float4* xp = reinterpret_cast<float4*>(it.xhat + base);
+#pragma unroll
+      for (int m = 0; m < NU; m += 2)
+        xp[m / 2] = make_float4(xo[m].x, xo[m].y, xo[m + 1].x, xo[m + 1].y);
+    }
+    if constexpr (NU == 4) {
+      if (it.mu) *reinterpret_cast<float4*>(it.mu + base) = make_float4(mo[0], mo[1], mo[2], mo[3]);
+      if (it.rho)
+        *reinterpret_cast<float4*>(it.rho + base) = make_float4(ro[0], ro[1], ro[2], ro[3]);
+    } else {
+      if (it.mu) *reinterpret_cast<float2*>(it.mu + base) = make_float2(mo[0], mo[1]);
+      if (it.rho) *reinterpret_cast<float2*>(it.rho + base) = make_float2(ro[0], ro[1]);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NU; ++m) {
+    const bool in = VEC || u0 + m < it.U;
+    if (!in) continue;
+    const bool valid = mo[m] > 0.f;
+    if (!valid) *flags |= ST_MU_NONPOS;
+    const int64_t o = base + m;
+    if constexpr (!VEC) {
+      if (it.xhat) it.xhat[o] = xo[m];
+      if (it.mu) it.mu[o] = mo[m];
+      if (it.rho) it.rho[o] = ro[m];
+    }
+    if (it.llr) {
+      float lI[H], lQ[H];
+      if (valid) {
+        const float inv = 1.f / mo[m];
+        axis_llr_t<H>(xo[m].x * inv, cq, ro[m], lI);
+        axis_llr_t<H>(xo[m].y * inv, cq, ro[m], lQ);
+      } else {
+#pragma unroll
+        for (int k = 0; k < H; ++k) lI[k] = lQ[k] = 0.f;
+      }
+      float2* lp = reinterpret_cast<float2*>(it.llr + o * QB);
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        const float a = 2 * k < H ? lI[2 * k] : lQ[2 * k - H];
+        const float b = 2 * k + 1 < H ? lI[2 * k + 1] : lQ[2 * k + 1 - H];
+        lp[k] = make_float2(a, b);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CG-D, one warp per instance
+// ---------------------------------------------------------------------------
+
+template <int UT, int EL, bool X3, bool VEC>
+__device__ __forceinline__ void detect_warp_instance(const DetItem& it, uint2* frag, float2* sAB,
+                                                     int* status) {
+  constexpr int NB = UT / 8;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float Gr[NB][4], Gi[NB][4], Mr[NB][4], Mn[NB][4];
+#pragma unroll
+  for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Gr[nt][k] = Gi[nt][k] = Mr[nt][k] = Mn[nt][k] = 0.f;
+
+  // ---- Algorithm 1 line 5: G and b^T on the tensor cores, loads one k-step ahead
+  const int KS = (it.B + 7) / 8;
+  float2 ha[4], ya[4], hb[4], yb[4];
+  load_h_ks<UT, VEC>(it.H, it.B, it.U, 0, g, t, ha);
+  load_y_ks<VEC>(it.Y, it.B, it.R, 0, g, t, ya);
+  for (int ks = 0; ks < KS; ks += 2) {  // ping-pong: loads run one k-step ahead
+    if (ks + 1 < KS) {
+      load_h_ks<UT, VEC>(it.H, it.B, it.U, ks + 1, g, t, hb);
+      load_y_ks<VEC>(it.Y, it.B, it.R, ks + 1, g, t, yb);
+    }
+    gram_ks<UT, EL, X3, true>(ha, ya, Gr, Gi, Mr, Mn);
+    if (ks + 1 >= KS) break;
+    if (ks + 2 < KS) {
+      load_h_ks<UT, VEC>(it.H, it.B, it.U, ks + 2, g, t, ha);
+      load_y_ks<VEC>(it.Y, it.B, it.R, ks + 2, g, t, ya);
+    }
+    gram_ks<UT, EL, X3, true>(hb, yb, Gr, Gi, Mr, Mn);
+  }
+
+  // ---- lines 7-16
+  WarpCg<UT, EL> cg;
+  float Gd[NB][2];
+  WarpCg<UT, EL>::setup_a(Gr, Gi, it.sigma, frag, cg.D, Gd);
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+        cg.res[hh][nt][c] = make_float2(Mr[nt][2 * hh + c], -Mn[nt][2 * hh + c]);
+  __syncwarp();
+  cg.template run<true>(frag, sAB, it.R, it.K);
+  __syncwarp();
+
+  // ---- line 19 and Eq. 4
+  int flags = 0;
+  const float cq = sqrtf(3.f * it.Es / (2.f * float((1 << it.q) - 1)));
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    const int r = g + 8 * hh;
+    if (r >= it.R) continue;
+    if (cg.broke[hh]) flags |= ST_BREAKDOWN;
+    float mu[NB][2], rho[NB][2], l[NB][2];
+    cg.tracker_l(sAB, hh, l);
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        mu[nt][c] = l[nt][c] * Gd[nt][c];          // Eq. 12
+        rho[nt][c] = Gd[nt][c] / it.N0;            // Eq. 13
+      }
+    switch (it.q) {
+      case 2: store_row_detect<UT, 2, VEC>(it, r, t, cg.v[hh], mu, rho, cq, &flags); break;
+      case 4: store_row_detect<UT, 4, VEC>(it, r, t, cg.v[hh], mu, rho, cq, &flags); break;
+      case 6: store_row_detect<UT, 6, VEC>(it, r, t, cg.v[hh], mu, rho, cq, &flags); break;
+      default: store_row_detect<UT, 8, VEC>(it, r, t, cg.v[hh], mu, rho, cq, &flags); break;
+    }
+  }
+  flags = __reduce_or_sync(0xffffffffu, flags);
+  if (lane == 0) {
+    if (it.status) *it.status = flags;
+    *status = flags;
+  }
+}
+
+// Whether an instance may take the vector paths (16-byte loads and stores).
+template <int UT>
+__device__ __forceinline__ bool detect_vec(const DetItem& it) {
+  return it.U == UT && (it.B % 2) == 0 && al16(it.H) && al16(it.Y) &&
+         (it.xhat == nullptr || al16(it.xhat)) && (it.mu == nullptr || al16(it.mu)) &&
+         (it.rho == nullptr || al16(it.rho)) && (it.llr == nullptr || al16(it.llr));
+}
+
+template <int UT, int EL, bool X3, class Src>
+__device__ __forceinline__ void detect_warp_body(const Src& src) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5;
+  unsigned char* mine = smem + warp * WarpCfg<UT>::WARP_BYTES;
+  uint2* frag = reinterpret_cast<uint2*>(mine);
+  float2* sAB = reinterpret_cast<float2*>(mine + WarpCfg<UT>::FRAG_BYTES);
+  const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+  int64_t cur = warp_first(src, int64_t(blockIdx.x) * (blockDim.x >> 5) + warp);
+  while (cur >= 0) {
+    const DetItem it = det_item(src, cur);
+    int st = 0;
+    if (detect_vec<UT>(it))
+      detect_warp_instance<UT, EL, X3, true>(it, frag, sAB, &st);
+    else
+      detect_warp_instance<UT, EL, X3, false>(it, frag, sAB, &st);
+    __syncwarp();
+    if constexpr (SrcTraits<Src>::kDyn) {
+      if ((threadIdx.x & 31) == 0) src_done(src, cur, st);
+    }
+    cur = warp_next(src, cur, nw);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CG-P, one warp per instance
+// ---------------------------------------------------------------------------
+
+template <int UT, int EL, bool X3, bool VEC>
+__device__ __forceinline__ void precode_warp_instance(const PreItem& it, uint2* frag, int* status) {
+  constexpr int NB = UT / 8;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float Gr[NB][4], Gi[NB][4], Mr[NB][4], Mn[NB][4];
+#pragma unroll
+  for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Gr[nt][k] = Gi[nt][k] = Mr[nt][k] = Mn[nt][k] = 0.f;
+
+  // ---- Algorithm 1 line 6: G on the tensor cores
+  const int KS = (it.B + 7) / 8;
+  float2 ha[4], hb[4];
+  const float2 y0[4] = {};
+  load_h_ks<UT, VEC>(it.H, it.B, it.U, 0, g, t, ha);
+  for (int ks = 0; ks < KS; ks += 2) {  // ping-pong: loads run one k-step ahead
+    if (ks + 1 < KS) load_h_ks<UT, VEC>(it.H, it.B, it.U, ks + 1, g, t, hb);
+    gram_ks<UT, EL, X3, false>(ha, y0, Gr, Gi, Mr, Mn);
+    if (ks + 1 >= KS) break;
+    if (ks + 2 < KS) load_h_ks<UT, VEC>(it.H, it.B, it.U, ks + 2, g, t, ha);
+    gram_ks<UT, EL, X3, false>(hb, y0, Gr, Gi, Mr, Mn);
+  }
+
+  // ---- lines 7-14 with b = t
+  WarpCg<UT, EL> cg;
+  float Gd[NB][2];
+  WarpCg<UT, EL>::setup_a(Gr, Gi, it.sigma, frag, cg.D, Gd);
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    const int r = g + 8 * hh;
+    const float2* tr = it.T + int64_t(r) * it.U;
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int u = pos_user<UT>(8 * nt + 2 * t + c);
+        cg.res[hh][nt][c] = (r < it.R && u < it.U) ? tr[u] : make_float2(0.f, 0.f);
+      }
+  }
+  __syncwarp();
+  cg.template run<false>(frag, nullptr, it.R, it.K);
+
+  // ||q||^2 = v^H (A - sigma I) v with one more product w = A v
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) cg.p[hh][nt][c] = cg.v[hh][nt][c];
+  float Er[NB][4], Ei[NB][4];
+  cg.matvec(frag, Er, Ei);
+  float qq[2] = {0.f, 0.f};
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float2 vv = cg.v[hh][nt][c];
+        const float wx = fmaf(-it.sigma, vv.x, Er[nt][2 * hh + c]);
+        const float wy = fmaf(-it.sigma, vv.y, Ei[nt][2 * hh + c]);
+        qq[hh] = fmaf(vv.x, wx, fmaf(vv.y, wy, qq[hh]));
+      }
+  quad_sum2(qq[0], qq[1]);
+  float inv[2];
+  int flags = 0;
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    const int r = g + 8 * hh;
+    const float nr = sqrtf(fmaxf(qq[hh], 0.f));
+    inv[hh] = it.normalize ? (nr > 0.f ? 1.f / nr : 0.f) : 1.f;
+    if (r < it.R) {
+      if (t == 0 && it.qnorm) it.qnorm[r] = nr;
+      if (cg.broke[hh]) flags |= ST_BREAKDOWN;
+    }
+  }
+
+  // ---- line 20: q = H v on the tensor cores, 8 antennas per n-tile
+  uint32_t vh[NB][4], vl[NB][4];
+#pragma unroll
+  for (int ks = 0; ks < NB; ++ks) {
+    const uint2 s0 = split_c<EL>(cg.v[0][ks][0]);
+    const uint2 s1 = split_c<EL>(cg.v[1][ks][0]);
+    const uint2 s2 = split_c<EL>(cg.v[0][ks][1]);
+    const uint2 s3 = split_c<EL>(cg.v[1][ks][1]);
+    vh[ks][0] = s0.x; vl[ks][0] = s0.y;
+    vh[ks][1] = s1.x; vl[ks][1] = s1.y;
+    vh[ks][2] = s2.x; vl[ks][2] = s2.y;
+    vh[ks][3] = s3.x; vl[ks][3] = s3.y;
+  }
+  const int NBQ = (it.B + 7) / 8;
+  for (int nb = 0; nb < NBQ; ++nb) {
+    const int b = 8 * nb + g;
+    // lane's H entries at its k-positions: e[ks][j] = H(b, user(8 ks + 2 t + j))
+    float2 e[NB][2];
+    const float2 z = make_float2(0.f, 0.f);
+    if constexpr (VEC) {
+      const bool ok = b < it.B;
+      if constexpr (UT == 16) {
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 f0 = ok ? ldg4(it.H + b * 16 + 4 * t) : zero4;      // users 4t, 4t+1
+        const float4 f1 = ok ? ldg4(it.H + b * 16 + 4 * t + 2) : zero4;  // users 4t+2, 4t+3
+        e[0][0] = make_float2(f0.x, f0.y);
+        e[1][0] = make_float2(f0.z, f0.w);
+        e[0][1] = make_float2(f1.x, f1.y);
+        e[1][1] = make_float2(f1.z, f1.w);
+      } else {
+        const float4 f0 = ok ? ldg4(it.H + b * 8 + 2 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        e[0][0] = make_float2(f0.x, f0.y);
+        e[0][1] = make_float2(f0.z, f0.w);
+      }
+    } else {
+#pragma unroll
+      for (int ks = 0; ks < NB; ++ks)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int u = pos_user<UT>(8 * ks + 2 * t + j);
+          e[ks][j] = (b < it.B && u < it.U) ? ldg2(it.H + b * it.U + u) : z;
+        }
+    }
+    float qr[4] = {0.f, 0.f, 0.f, 0.f}, qi[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int ks = 0; ks < NB; ++ks) {
+      const uint2 s0 = split_c<EL>(e[ks][0]), s1 = split_c<EL>(e[ks][1]);
+      // real part: v . conj(H); imaginary part: v . (Hi, Hr)
+      mma_split<EL, X3>(qr, vh[ks], vl[ks], neg_hi(s0.x), neg_hi(s1.x), neg_hi(s0.y),
+                        neg_hi(s1.y));
+      mma_split<EL, X3>(qi, vh[ks], vl[ks], swap_halves(s0.x), swap_halves(s1.x),
+                        swap_halves(s0.y), swap_halves(s1.y));
+    }
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int r = g + 8 * hh;
+      if (r >= it.R) continue;
+      const int b0 = 8 * nb + 2 * t;
+      const float2 q0 = make_float2(qr[2 * hh] * inv[hh], qi[2 * hh] * inv[hh]);
+      const float2 q1 = make_float2(qr[2 * hh + 1] * inv[hh], qi[2 * hh + 1] * inv[hh]);
+      float2* qrow = it.q + int64_t(r) * it.B;
+      if constexpr (VEC) {
+        if (b0 < it.B)
+          *reinterpret_cast<float4*>(qrow + b0) = make_float4(q0.x, q0.y, q1.x, q1.y);
+      } else {
+        if (b0 < it.B) qrow[b0] = q0;
+        if (b0 + 1 < it.B) qrow[b0 + 1] = q1;
+      }
+    }
+  }
+  flags = __reduce_or_sync(0xffffffffu, flags);
+  if (lane == 0) {
+    if (it.status) *it.status = flags;
+    *status = flags;
+  }
+}
+
+// Whether an instance may take the vector paths.
+template <int UT>
+__device__ __forceinline__ bool precode_vec(const PreItem& it) {
+  return it.U == UT && (it.B % 2) == 0 && al16(it.H) && al16(it.q);
+}
+
+template <int UT, int EL, bool X3, class Src>
+__device__ __forceinline__ void precode_warp_body(const Src& src) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5;
+  uint2* frag = reinterpret_cast<uint2*>(smem + warp * WarpCfg<UT>::WARP_BYTES);
+  const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+  int64_t cur = warp_first(src, int64_t(blockIdx.x) * (blockDim.x >> 5) + warp);
+  while (cur >= 0) {
+    const PreItem it = pre_item(src, cur);
+    int st = 0;
+    if (precode_vec<UT>(it))
+      precode_warp_instance<UT, EL, X3, true>(it, frag, &st);
+    else
+      precode_warp_instance<UT, EL, X3, false>(it, frag, &st);
+    __syncwarp();
+    if constexpr (SrcTraits<Src>::kDyn) {
+      if ((threadIdx.x & 31) == 0) src_done(src, cur, st);
+    }
+    cur = warp_next(src, cur, nw);
+  }
+}
+
+template <int UT, int EL, bool X3>
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB) detect_warp_kernel(const DetectArgs a) {
+  detect_warp_body<UT, EL, X3>(a);
+}
+template <int UT, int EL, bool X3>
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB) precode_warp_kernel(const PrecodeArgs a) {
+  precode_warp_body<UT, EL, X3>(a);
+}
+template <int UT, int EL, bool X3>
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB) detect_warp_batch_kernel(const BatchArgs b) {
+  detect_warp_body<UT, EL, X3>(b);
+}
+template <int UT, int EL, bool X3>
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB)
+    precode_warp_batch_kernel(const BatchArgs b) {
+  precode_warp_body<UT, EL, X3>(b);
+}
+template <int UT, int EL, bool X3>
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB) detect_warp_serve_kernel(const ServeArgs s) {
+  detect_warp_body<UT, EL, X3>(s);
+}
+template <int UT, int EL, bool X3>
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB)
+    precode_warp_serve_kernel(const ServeArgs s) {
+  precode_warp_body<UT, EL, X3>(s);
+}
+
+}  // namespace cgm

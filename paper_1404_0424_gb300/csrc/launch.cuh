@@ -43,6 +43,15 @@ cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const Ba
 cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
                             cudaStream_t st, bool launch, uint32_t* smem_out, int* resident_out);
 
+// Warp-per-instance kernels (warp.cu): padded users 8 or 16, approximate
+// tracker only. Batch and serve forms as above (grid in CTAs of 4 warps).
+cudaError_t launch_detect_warp(int UT, int el, bool x3, const DetectArgs& a, cudaStream_t s);
+cudaError_t launch_precode_warp(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s);
+cudaError_t launch_batch_warp(int op, int UT, int el, bool x3, const BatchArgs& b, int max_grid,
+                              cudaStream_t s, bool launch, int* grid_out);
+cudaError_t launch_serve_warp(int op, int UT, int el, bool x3, const ServeArgs& sa, int grid,
+                              cudaStream_t s, bool launch, int* resident_out);
+
 // Dynamic shared memory of one CTA for the given shape (bytes).
 uint32_t detect_smem_bytes(int UT, int B, int U, int R, int exact);
 uint32_t precode_smem_bytes(int UT, int B, int U, int R);

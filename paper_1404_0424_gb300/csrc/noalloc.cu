@@ -16,7 +16,9 @@ namespace {
 constexpr size_t kDescBytes = sizeof(cg_desc) * CG_STATIC_MAX_PROBLEMS;
 constexpr size_t kWorkOff = (kDescBytes + 255) & ~size_t(255);
 constexpr size_t kWorkBytes = sizeof(int2) * CG_STATIC_MAX_INSTANCES;
-constexpr int kMaxBins = 12;  // 2 operations x 3 padded user counts x FULL or not
+// 2 operations x 3 padded user counts x FULL or not, plus exact-tracker
+// detection with 8 or 16 padded users x FULL or not
+constexpr int kMaxBins = 16;
 constexpr size_t kCountOff = (kWorkOff + kWorkBytes + 255) & ~size_t(255);
 constexpr size_t kScratchBytes = kCountOff + sizeof(unsigned long long) * kMaxBins;
 static_assert(kScratchBytes <= (size_t(1) << 20), "static scratch stays within 1 MiB");
@@ -71,7 +73,10 @@ struct StaticBin {
 int bin_of(const cg_desc& d, int* UT, int* full) {
   *UT = padded_users(d.U) < 8 ? 8 : padded_users(d.U);
   *full = (d.U == *UT && d.B % 8 == 0) ? 1 : 0;
-  return (d.op * 3 + (*UT == 8 ? 0 : *UT == 16 ? 1 : 2)) * 2 + *full;
+  const int uti = *UT == 8 ? 0 : *UT == 16 ? 1 : 2;
+  if (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT && uti < 2)
+    return 12 + uti * 2 + *full;
+  return (d.op * 3 + uti) * 2 + *full;
 }
 
 }  // namespace
@@ -98,7 +103,7 @@ extern "C" int cg_batch_run_static(const cg_desc* descs, int64_t n, int32_t prec
 
   // bins: count, offsets, then fill the host staging of the work units
   StaticBin bins[kMaxBins];
-  for (int b = 0; b < kMaxBins; ++b) bins[b] = StaticBin{b / 6, 0, b & 1, 0, 0, 0, 0, 0};
+  for (int b = 0; b < kMaxBins; ++b) bins[b] = StaticBin{b < 12 ? b / 6 : 0, 0, b & 1, 0, 0, 0, 0, 0};
   for (int64_t i = 0; i < n; ++i) {
     int UT, full;
     StaticBin& b = bins[bin_of(descs[i], &UT, &full)];

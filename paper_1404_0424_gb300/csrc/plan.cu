@@ -197,14 +197,17 @@ int cg_plan_create(const cg_desc* descs, int64_t n, int32_t precision, void* str
     delete p;
     return CG_ECUDA;
   }
-  // bins by (operation, padded users, FULL); each keeps its largest B and R
-  std::map<std::tuple<int, int, int>, size_t> index;
+  // bins by (operation, padded users, FULL, exact tracker); each keeps its
+  // largest B and R. Exact-tracker detection has bins of its own so that
+  // the other problems keep the warp-per-instance kernels.
+  std::map<std::tuple<int, int, int, int>, size_t> index;
   for (int64_t i = 0; i < n; ++i) {
     const cg_desc& d = descs[i];
     if (d.n_inst == 0) continue;
     const int UT = std::max(8, padded_users(d.U));
     const bool full = d.U == UT && d.B % 8 == 0;
-    const auto key = std::make_tuple(d.op, UT, int(full));
+    const int exact = (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT) ? 1 : 0;
+    const auto key = std::make_tuple(d.op, UT, int(full), exact);
     auto it = index.find(key);
     if (it == index.end()) {
       index[key] = p->bins.size();

@@ -25,9 +25,13 @@ int64_t mono_ns() {
   return int64_t(ts.tv_sec) * 1000000000LL + ts.tv_nsec;
 }
 
+// Class of a request: (operation, padded users 8 / 16 / 32). Detection with
+// the exact tracker runs in the (detect, 32) class, whose CTA kernel has the
+// shared memory for it; the 8- and 16-user classes run one warp per instance.
 int class_of(const cg_desc& d, int* UT) {
   const int pu = padded_users(d.U);
   *UT = pu < 8 ? 8 : pu;
+  if (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT) *UT = 32;
   return d.op * 3 + (*UT == 8 ? 0 : *UT == 16 ? 1 : 2);
 }
 
@@ -88,7 +92,7 @@ ServeArgs args_for(const cg_server* s, int cls) {
   a.cap = s->cfg.capacity;
   a.PB = s->cfg.max_B;
   a.PR = s->cfg.max_R;
-  a.PEX = cls < 3 ? 1 : 0;
+  a.PEX = cls == 2 ? 1 : 0;
   a.idle_ns = (unsigned long long)s->cfg.idle_timeout_ms * 1000000ull;
   return a;
 }

@@ -198,6 +198,10 @@ cudaError_t batch_ut(int op, int el, bool x3, bool full, const BatchArgs& b, int
 cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const BatchArgs& b,
                             int max_grid, cudaStream_t s, bool launch, uint32_t* smem_out,
                             int* grid_out) {
+  if (UT <= 16 && b.PEX == 0) {  // warp-per-instance kernels
+    if (smem_out) *smem_out = 0;
+    return launch_batch_warp(op, UT, el, x3, b, max_grid, s, launch, grid_out);
+  }
   switch (UT) {
     case 4:
     case 8: return batch_ut<8>(op, el, x3, full, b, max_grid, s, launch, smem_out, grid_out);
@@ -252,6 +256,10 @@ cudaError_t serve_ut(int op, int el, bool x3, const ServeArgs& s, int grid, cuda
 
 cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
                             cudaStream_t st, bool launch, uint32_t* smem_out, int* resident_out) {
+  if (UT <= 16 && s.PEX == 0) {  // warp-per-instance kernels
+    if (smem_out) *smem_out = 0;
+    return launch_serve_warp(op, UT, el, x3, s, grid, st, launch, resident_out);
+  }
   switch (UT) {
     case 8: return serve_ut<8>(op, el, x3, s, grid, st, launch, smem_out, resident_out);
     case 16: return serve_ut<16>(op, el, x3, s, grid, st, launch, smem_out, resident_out);
