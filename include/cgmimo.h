@@ -67,8 +67,17 @@ extern "C" {
 #define CG_SINR_APPROX 0  /* Eqs. 11-13: diagonal recursion, rho = G_ii / N0 */
 #define CG_SINR_EXACT 1   /* Eq. 10 and the B = L_K G, C = B L_K^H expressions */
 
-/* How e = A p is formed inside Algorithm 1 (line 9). */
-#define CG_AMUL_AUTO 0      /* library choice */
+/* How e = A p is formed inside Algorithm 1 (line 9).
+ * CG_AMUL_IMPLICIT forms no Gram: each product costs 2 B U complex
+ * multiply-adds per right-hand side, done in FP32 on the CUDA cores whatever
+ * the precision field says (there is no Gram, and the matched filter is an
+ * FP32 sum). It does not combine with
+ * CG_SINR_EXACT (CG_ENOTSUP), whose expressions need the Gram.
+ * CG_AMUL_AUTO picks the implicit product on the FP32 path when it is the
+ * cheaper one, 4 K R < U + 1 (the Hermitian Gram costs B U (U + 1) / 2 per
+ * instance), and the explicit Gram otherwise and on the tensor-core paths.
+ * The batched and serving entry points always form the Gram. */
+#define CG_AMUL_AUTO 0      /* library choice (above) */
 #define CG_AMUL_EXPLICIT 1  /* form A = H^H H + (N0/Es) I once per instance */
 #define CG_AMUL_IMPLICIT 2  /* e = H^H (H p) + (N0/Es) p, two matrix-vector products */
 
@@ -200,8 +209,10 @@ int cg_plan_destroy(cg_plan* plan);
  *   hbm_budget_bytes  admission limit: input + output bytes of admitted,
  *                     unfinished requests (a request larger than it is CG_ETOOBIG)
  *   max_B, max_R      largest B and R a request may have (they size the kernels)
- *   ctas_per_class    persistent CTAs of each class kernel; 0 = an equal share of
- *                     the resident CTAs among the six classes
+ *   ctas_per_class    persistent work units (CTAs) of each class kernel; 0 = a
+ *                     share of the SMs per class in proportion to the cost of
+ *                     one of its instances (weights 1, 2, 8 for 8, 16 and 32
+ *                     padded users, for each operation)
  *   idle_timeout_ms   a class kernel exits after this long without work and is
  *                     relaunched by the next submit or poll that needs it          */
 typedef struct cg_serve_cfg {
@@ -242,7 +253,11 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out);
  * exceeds the budget or has 2^24 instances or more; on success *ticket
  * identifies it. A request's bytes count against the budget until it
  * completes; its ring slot stays in use until a cg_serve_poll has reported
- * it done, so poll every ticket until done. Slots are freed in ticket order. */
+ * it done, so poll every ticket until done. Slots are freed in ticket order.
+ * The server's kernels run on streams of their own and may start on the
+ * request at once: its inputs must already hold their values, and no other
+ * work may touch its outputs, when submit is called (synchronise the stream
+ * that produced them first). */
 int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket);
 
 /* *done = 1 once every instance of the request is finished and its outputs

@@ -41,9 +41,10 @@ using namespace cgm;
 
 namespace {
 
-// Modes implemented by this build.
+// Modes implemented by this build: the exact tracker needs the Gram, so it
+// does not combine with the implicit product.
 int check_supported(const cg_params* p) {
-  if (p->amul_mode == CG_AMUL_IMPLICIT) return CG_ENOTSUP;
+  if (p->amul_mode == CG_AMUL_IMPLICIT && p->sinr_mode == CG_SINR_EXACT) return CG_ENOTSUP;
   return CG_OK;
 }
 
@@ -75,7 +76,9 @@ int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void*
   a.exact = p->sinr_mode == CG_SINR_EXACT;
   a.bulk = (p->B % 2 == 0) && aligned(H, 16) && aligned(Y, 16);
   cudaError_t err;
-  if (p->precision == CG_PREC_FP32) {
+  if (use_implicit(p->amul_mode, p->precision, p->K, p->R, p->U, a.exact)) {
+    err = launch_detect_implicit(padded_users(p->U), a, s);
+  } else if (p->precision == CG_PREC_FP32) {
     err = launch_detect(padded_users(p->U), a, s, nullptr);
   } else {
     int el;
@@ -109,7 +112,9 @@ int precode_device(const cg_params* p, int64_t n_inst, const void* H, const void
   a.bulk_h = ((p->B * p->U) % 2 == 0) && aligned(H, 16);
   a.bulk_t = ((p->R * p->U) % 2 == 0) && aligned(T, 16);
   cudaError_t err;
-  if (p->precision == CG_PREC_FP32) {
+  if (use_implicit(p->amul_mode, p->precision, p->K, p->R, p->U, false)) {
+    err = launch_precode_implicit(padded_users(p->U), a, s);
+  } else if (p->precision == CG_PREC_FP32) {
     err = launch_precode(padded_users(p->U), a, s, nullptr);
   } else {
     int el;

@@ -321,23 +321,40 @@ struct ServeCompletion {
   int pad;
 };
 
-// Host-written control block in mapped host memory.
+// Control block in mapped host memory: the stop flag (host-written), and per
+// class the number of running work units (CTAs or warps) and the launch
+// generation whose last unit has exited (device-written), which let the host
+// see whether a class kernel is alive without a CUDA call.
 struct ServeCtrl {
-  unsigned long long class_tail[8];  // requests published per class
   int stop;
-  int pad[3];
+  int pad;
+  int live[8];
+  unsigned long long exited_gen[8];
 };
 
 struct ServeArgs {
   ServeSlot* slots;             // device, one per ring slot
-  const unsigned long long* class_ring;  // mapped host: [class][cap] published entries
-  const ServeCtrl* ctrl;        // mapped host
+  const unsigned long long* class_ring;  // device: [class][cap] published entries
+  const unsigned long long* class_tail;  // device: requests published per class
+  ServeCtrl* ctrl;              // mapped host
   ServeCompletion* comp;        // mapped host, one per ring slot
   unsigned long long* class_head;  // device: first request of the class with work left
   int cls, cap;
   int PB, PR, PEX;
   unsigned long long idle_ns;   // exit after this long without work
+  unsigned long long gen;       // launch generation of this kernel
 };
+
+// A work unit (CTA or warp, one thread calls) starts or ends serving its
+// class. The unit that brings the count to zero records the generation.
+__device__ __forceinline__ void serve_unit_enter(const ServeArgs& s) {
+  atomicAdd_system(&s.ctrl->live[s.cls], 1);
+}
+__device__ __forceinline__ void serve_unit_exit(const ServeArgs& s) {
+  __threadfence_system();
+  if (atomicSub_system(&s.ctrl->live[s.cls], 1) == 1)
+    atomicMax_system(&s.ctrl->exited_gen[s.cls], s.gen);
+}
 
 template <class T>
 __device__ __forceinline__ T volatile_load(const T* p) {
@@ -379,7 +396,7 @@ __device__ __forceinline__ int64_t serve_claim_wait(const ServeArgs& s) {
   while (true) {
     if (volatile_load(&s.ctrl->stop)) return -1;
     const unsigned long long head = volatile_load(&s.class_head[s.cls]);
-    const unsigned long long tail = volatile_load(&s.ctrl->class_tail[s.cls]);
+    const unsigned long long tail = volatile_load(&s.class_tail[s.cls]);
     if (head < tail) {
       const int64_t w = serve_claim_at(s, head);
       if (w >= 0) return w;
@@ -396,26 +413,23 @@ __device__ __forceinline__ void claim_next(const ServeArgs& s, int64_t* slot) {
   *slot = serve_claim_wait(s);
 }
 
-// Non-blocking form: -2 when no work is available yet (try again later).
+// Non-blocking claim by one thread: -2 when no work is available yet (try
+// again later), -1 on the stop flag.
+__device__ __forceinline__ int64_t serve_claim_try(const ServeArgs& s) {
+  while (true) {
+    if (volatile_load(&s.ctrl->stop)) return -1;
+    const unsigned long long head = volatile_load(&s.class_head[s.cls]);
+    const unsigned long long tail = volatile_load(&s.class_tail[s.cls]);
+    if (head >= tail) return -2;
+    const int64_t w = serve_claim_at(s, head);
+    if (w >= 0) return w;
+  }
+}
+
+// Thread 0 of a CTA, non-blocking (serve_claim_try) into shared memory.
 __device__ __forceinline__ void claim_try(const ServeArgs& s, int64_t* slot) {
   if (threadIdx.x != 0) return;
-  while (true) {
-    if (volatile_load(&s.ctrl->stop)) {
-      *slot = -1;
-      return;
-    }
-    const unsigned long long head = volatile_load(&s.class_head[s.cls]);
-    const unsigned long long tail = volatile_load(&s.ctrl->class_tail[s.cls]);
-    if (head >= tail) {
-      *slot = -2;
-      return;
-    }
-    const int64_t w = serve_claim_at(s, head);
-    if (w >= 0) {
-      *slot = w;
-      return;
-    }
-  }
+  *slot = serve_claim_try(s);
 }
 
 // Copy of a slot's descriptor read at L2 (bypassing L1, which may still hold
@@ -1524,13 +1538,17 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
 template <int UT, int EL, bool X3>
 __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
     detect_tc_serve_kernel(const ServeArgs s) {
+  if (threadIdx.x == 0) serve_unit_enter(s);
   detect_tc_body<UT, EL, X3, false>(s, s.PB, UT, s.PR, s.PEX);
+  if (threadIdx.x == 0) serve_unit_exit(s);
 }
 
 template <int UT, int EL, bool X3>
 __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
     precode_tc_serve_kernel(const ServeArgs s) {
+  if (threadIdx.x == 0) serve_unit_enter(s);
   precode_tc_body<UT, EL, X3, false>(s, s.PB, UT, s.PR);
+  if (threadIdx.x == 0) serve_unit_exit(s);
 }
 
 }  // namespace cgm

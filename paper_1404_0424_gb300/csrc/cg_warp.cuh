@@ -30,6 +30,9 @@
 
 namespace cgm {
 
+// Load stages in flight per warp (16-byte cp.async copies into a ring).
+constexpr int RING_STAGES = 4;
+
 template <int UT>
 struct WarpCfg {
   static_assert(UT == 8 || UT == 16, "warp kernels serve 8 or 16 padded users");
@@ -37,12 +40,15 @@ struct WarpCfg {
   static constexpr int NFRAG = NB * NB * 2 * 2;  // CG B fragments: (ks, nt, b0/b1, re/im)
   static constexpr int WARPS = 4;       // warps per CTA (independent)
   static constexpr int NTHR = 32 * WARPS;
-  // per warp: the CG B fragments (one uint2 per lane and fragment), then
-  // alpha_k, beta_k of the 16 right-hand-side rows for the tracker
+  // per warp: a ring of RING_STAGES load stages (4 planes of 16 bytes per
+  // lane each), the CG B fragments (one uint2 per lane and fragment), and
+  // alpha_k, beta_k of the 16 right-hand-side rows for the tracker (K <= UT)
+  static constexpr uint32_t RING_BYTES = uint32_t(RING_STAGES) * 4u * 32u * 16u;
   static constexpr uint32_t FRAG_BYTES = uint32_t(NFRAG) * 32u * 8u;
-  static constexpr uint32_t AB_BYTES = uint32_t(KMAX) * 16u * 2u * 4u;
-  static constexpr uint32_t WARP_BYTES = FRAG_BYTES + AB_BYTES;
-  static constexpr uint32_t SMEM = uint32_t(WARPS) * WARP_BYTES;
+  static constexpr uint32_t AB_BYTES = uint32_t(UT) * 16u * 8u;
+  static constexpr uint32_t WARP_BYTES = RING_BYTES + FRAG_BYTES + AB_BYTES;
+  static constexpr uint32_t SMEM = uint32_t(WARPS) * WARP_BYTES;       // CG-D
+  static constexpr uint32_t PRE_SMEM = uint32_t(WARPS) * FRAG_BYTES;  // CG-P: fragments only
 };
 
 template <int UT>
@@ -54,6 +60,107 @@ __device__ __forceinline__ float4 ldg4(const float2* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
 }
 __device__ __forceinline__ float2 ldg2(const float2* p) { return __ldg(p); }
+
+// Asynchronous global -> shared copies (16 or 8 bytes), zero-filled when
+// !ok (src is then not read). Completion is tracked per thread in groups.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(ok ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(ok ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Stage `slot` of a warp ring: plane j of lane l at ring + (slot*4 + j)*512 + 16 l.
+__device__ __forceinline__ unsigned char* ring_at(unsigned char* ring, int slot, int plane) {
+  return ring + (slot * 4 + plane) * 512 + (threadIdx.x & 31) * 16;
+}
+
+// Issues one Gram k-step (antennas 8 ks + 2t, +1) into the ring: planes 0-1
+// the lane's H fragments, planes 2-3 (MF) its Y fragments; then commits a
+// group (an empty one when ks >= KS, which keeps the group count uniform).
+// Only the vector layout (U == UT, B even, 16-byte aligned) comes here.
+template <int UT, bool MF>
+__device__ __forceinline__ void ring_gram_issue(unsigned char* ring, const float2* H,
+                                                const float2* Y, int B, int R, int KS, int ks) {
+  if (ks < KS) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int slot = ks % RING_STAGES;
+    const int b0 = 8 * ks + 2 * t, b1 = b0 + 1;
+    const bool ok = b0 < B;
+    if constexpr (UT == 16) {
+      cp_async16(ring_at(ring, slot, 0), ok ? H + b0 * 16 + 2 * g : H, ok);
+      cp_async16(ring_at(ring, slot, 1), ok ? H + b1 * 16 + 2 * g : H, ok);
+    } else {
+      cp_async8(ring_at(ring, slot, 0), ok ? H + b0 * 8 + g : H, ok);
+      cp_async8(ring_at(ring, slot, 1), ok ? H + b1 * 8 + g : H, ok);
+    }
+    if constexpr (MF) {
+      const bool ok0 = ok && g < R, ok1 = ok && g + 8 < R;
+      cp_async16(ring_at(ring, slot, 2), ok0 ? Y + g * B + b0 : Y, ok0);
+      cp_async16(ring_at(ring, slot, 3), ok1 ? Y + (g + 8) * B + b0 : Y, ok1);
+    }
+  }
+  cp_commit();
+}
+
+template <int UT, bool MF>
+__device__ __forceinline__ void ring_gram_read(unsigned char* ring, int ks, float2 (&h)[4],
+                                               float2 (&y)[4]) {
+  const int slot = ks % RING_STAGES;
+  if constexpr (UT == 16) {
+    const float4 v0 = *reinterpret_cast<const float4*>(ring_at(ring, slot, 0));
+    const float4 v1 = *reinterpret_cast<const float4*>(ring_at(ring, slot, 1));
+    h[0] = make_float2(v0.x, v0.y);
+    h[1] = make_float2(v0.z, v0.w);
+    h[2] = make_float2(v1.x, v1.y);
+    h[3] = make_float2(v1.z, v1.w);
+  } else {
+    h[0] = *reinterpret_cast<const float2*>(ring_at(ring, slot, 0));
+    h[2] = *reinterpret_cast<const float2*>(ring_at(ring, slot, 1));
+    h[1] = h[3] = make_float2(0.f, 0.f);
+  }
+  if constexpr (MF) {
+    const float4 w0 = *reinterpret_cast<const float4*>(ring_at(ring, slot, 2));
+    const float4 w1 = *reinterpret_cast<const float4*>(ring_at(ring, slot, 3));
+    y[0] = make_float2(w0.x, w0.y);
+    y[2] = make_float2(w0.z, w0.w);
+    y[1] = make_float2(w1.x, w1.y);
+    y[3] = make_float2(w1.z, w1.w);
+  }
+}
+
+// First RING_STAGES - 1 k-steps of an instance's Gram.
+template <int UT, bool MF>
+__device__ __forceinline__ void ring_gram_prologue(unsigned char* ring, const float2* H,
+                                                   const float2* Y, int B, int R) {
+  const int KS = (B + 7) / 8;
+#pragma unroll
+  for (int ks = 0; ks < RING_STAGES - 1; ++ks) ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, ks);
+}
+
+// q = H v n-tile nb (antennas 8 nb + g): the lane's H entries of users
+// 4t..4t+3 (16 users: two 16-byte loads) or 2t..2t+1 (8 users: one).
+template <int UT>
+__device__ __forceinline__ void q_load(const float2* H, int B, int nb, int g, int t, float4& f0,
+                                       float4& f1) {
+  const int b = 8 * nb + g;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (b < B) {
+    f0 = ldg4(H + b * UT + (UT == 16 ? 4 : 2) * t);
+    f1 = UT == 16 ? ldg4(H + b * UT + 4 * t + 2) : zero4;
+  } else {
+    f0 = f1 = zero4;
+  }
+}
 
 // Compensated butterfly over the four lanes of a quad (lane bits 0 and 1)
 // for two independent sums.
@@ -435,14 +542,6 @@ __device__ __forceinline__ int64_t warp_first(const S& s, int64_t gw) {
   }
 }
 
-template <class S>
-__device__ __forceinline__ int64_t warp_next(const S& s, int64_t cur, int64_t nw) {
-  if constexpr (SrcTraits<S>::kDyn) {
-    return warp_claim(s);
-  } else {
-    return cur + nw < src_count(s) ? cur + nw : -1;
-  }
-}
 
 __device__ __forceinline__ bool al16(const void* p) {
   return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
@@ -451,6 +550,42 @@ __device__ __forceinline__ bool al16(const void* p) {
 // ---------------------------------------------------------------------------
 // Stores of one lane's detection outputs
 // ---------------------------------------------------------------------------
+
+// Max-log LLRs of Eq. 4 on one axis of square Gray QAM, from u = x / c.
+// With the levels a_j = k_j c, k_j = 2j - (L - 1), the squared distance is
+// c^2 (u^2 + k_j^2 - 2 k_j u); u^2 cancels in the difference of the two
+// minima, so only f_j = k_j^2 - 2 k_j u is formed (one FMA per level). Gray
+// bit m (counted from the least significant) is constant on aligned blocks
+// of 2^m levels and alternates over blocks as (i & 1) ^ (i >> 1 & 1), so its
+// two minima are taken over block minima built level by level.
+// out[t] (bit t, most significant first) = scale (min_0 f - min_1 f).
+template <int H>
+__device__ __forceinline__ void axis_llr_gray(float u, float scale, float (&out)[H]) {
+  constexpr int L = 1 << H;
+  float lvl[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const float k = float(2 * j - (L - 1));
+    lvl[j] = fmaf(-2.f * k, u, k * k);
+  }
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    const int nb = L >> m;
+    float m0 = INFINITY, m1 = INFINITY;
+#pragma unroll
+    for (int i = 0; i < nb; ++i) {
+      if (((i & 1) ^ ((i >> 1) & 1)) != 0)
+        m1 = fminf(m1, lvl[i]);
+      else
+        m0 = fminf(m0, lvl[i]);
+    }
+    out[H - 1 - m] = scale * (m0 - m1);
+    if (m + 1 < H) {
+#pragma unroll
+      for (int i = 0; i < nb / 2; ++i) lvl[i] = fminf(lvl[2 * i], lvl[2 * i + 1]);
+    }
+  }
+}
 
 // The 2 NB users of a lane in one right-hand-side row, in memory order
 // (16 users: 4t + m holds position (nt, c) = (m & 1, m >> 1); 8 users:
@@ -504,9 +639,10 @@ __device__ __forceinline__ void store_row_detect(const DetItem& it, int r, int t
     if (it.llr) {
       float lI[H], lQ[H];
       if (valid) {
-        const float inv = 1.f / mo[m];
-        axis_llr_t<H>(xo[m].x * inv, cq, ro[m], lI);
-        axis_llr_t<H>(xo[m].y * inv, cq, ro[m], lQ);
+        const float inv = __frcp_rn(mo[m] * cq);  // u = x_hat / (mu c)
+        const float scale = ro[m] * cq * cq;
+        axis_llr_gray<H>(xo[m].x * inv, scale, lI);
+        axis_llr_gray<H>(xo[m].y * inv, scale, lQ);
       } else {
 #pragma unroll
         for (int k = 0; k < H; ++k) lI[k] = lQ[k] = 0.f;
@@ -526,37 +662,62 @@ __device__ __forceinline__ void store_row_detect(const DetItem& it, int r, int t
 // CG-D, one warp per instance
 // ---------------------------------------------------------------------------
 
-template <int UT, int EL, bool X3, bool VEC>
-__device__ __forceinline__ void detect_warp_instance(const DetItem& it, uint2* frag, float2* sAB,
-                                                     int* status) {
+// Loading scheme of a Gram: the warp's cp.async ring (its prologue already
+// issued, RING_STAGES - 1 k-steps ahead), 16-byte register loads one k-step
+// ahead (through L1), or predicated element loads for any layout.
+enum : int { LD_RING = 0, LD_VEC = 1, LD_ELEM = 2 };
+
+// Algorithm 1 line 5: G and b^T on the tensor cores.
+template <int UT, int EL, bool X3, int LD, bool MF>
+__device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int B, int U, int R,
+                                          unsigned char* ring, float (&Gr)[UT / 8][4],
+                                          float (&Gi)[UT / 8][4], float (&Mr)[UT / 8][4],
+                                          float (&Mn)[UT / 8][4]) {
   constexpr int NB = UT / 8;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float Gr[NB][4], Gi[NB][4], Mr[NB][4], Mn[NB][4];
 #pragma unroll
   for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
     for (int k = 0; k < 4; ++k) Gr[nt][k] = Gi[nt][k] = Mr[nt][k] = Mn[nt][k] = 0.f;
-
-  // ---- Algorithm 1 line 5: G and b^T on the tensor cores, loads one k-step ahead
-  const int KS = (it.B + 7) / 8;
-  float2 ha[4], ya[4], hb[4], yb[4];
-  load_h_ks<UT, VEC>(it.H, it.B, it.U, 0, g, t, ha);
-  load_y_ks<VEC>(it.Y, it.B, it.R, 0, g, t, ya);
-  for (int ks = 0; ks < KS; ks += 2) {  // ping-pong: loads run one k-step ahead
-    if (ks + 1 < KS) {
-      load_h_ks<UT, VEC>(it.H, it.B, it.U, ks + 1, g, t, hb);
-      load_y_ks<VEC>(it.Y, it.B, it.R, ks + 1, g, t, yb);
+  const int KS = (B + 7) / 8;
+  if constexpr (LD == LD_RING) {
+    for (int ks = 0; ks < KS; ++ks) {
+      ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, ks + RING_STAGES - 1);
+      cp_wait<RING_STAGES - 1>();
+      float2 h[4], y[4];
+      ring_gram_read<UT, MF>(ring, ks, h, y);
+      gram_ks<UT, EL, X3, MF>(h, y, Gr, Gi, Mr, Mn);
     }
-    gram_ks<UT, EL, X3, true>(ha, ya, Gr, Gi, Mr, Mn);
-    if (ks + 1 >= KS) break;
-    if (ks + 2 < KS) {
-      load_h_ks<UT, VEC>(it.H, it.B, it.U, ks + 2, g, t, ha);
-      load_y_ks<VEC>(it.Y, it.B, it.R, ks + 2, g, t, ya);
+  } else {
+    constexpr bool V = LD == LD_VEC;
+    float2 ha[4], ya[4] = {}, hb[4], yb[4] = {};
+    load_h_ks<UT, V>(H, B, U, 0, g, t, ha);
+    if constexpr (MF) load_y_ks<V>(Y, B, R, 0, g, t, ya);
+    for (int ks = 0; ks < KS; ks += 2) {  // ping-pong: loads run one k-step ahead
+      if (ks + 1 < KS) {
+        load_h_ks<UT, V>(H, B, U, ks + 1, g, t, hb);
+        if constexpr (MF) load_y_ks<V>(Y, B, R, ks + 1, g, t, yb);
+      }
+      gram_ks<UT, EL, X3, MF>(ha, ya, Gr, Gi, Mr, Mn);
+      if (ks + 1 >= KS) break;
+      if (ks + 2 < KS) {
+        load_h_ks<UT, V>(H, B, U, ks + 2, g, t, ha);
+        if constexpr (MF) load_y_ks<V>(Y, B, R, ks + 2, g, t, ya);
+      }
+      gram_ks<UT, EL, X3, MF>(hb, yb, Gr, Gi, Mr, Mn);
     }
-    gram_ks<UT, EL, X3, true>(hb, yb, Gr, Gi, Mr, Mn);
   }
+}
 
-  // ---- lines 7-16
+// Lines 7-19 and Eq. 4 of one instance whose Gram and matched filters are done.
+template <int UT, int EL, bool VEC>
+__device__ __forceinline__ int detect_warp_finish(const DetItem& it, uint2* frag, float2* sAB,
+                                                  const float (&Gr)[UT / 8][4],
+                                                  const float (&Gi)[UT / 8][4],
+                                                  const float (&Mr)[UT / 8][4],
+                                                  const float (&Mn)[UT / 8][4]) {
+  constexpr int NB = UT / 8;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   WarpCg<UT, EL> cg;
   float Gd[NB][2];
   WarpCg<UT, EL>::setup_a(Gr, Gi, it.sigma, frag, cg.D, Gd);
@@ -571,23 +732,24 @@ __device__ __forceinline__ void detect_warp_instance(const DetItem& it, uint2* f
   cg.template run<true>(frag, sAB, it.R, it.K);
   __syncwarp();
 
-  // ---- line 19 and Eq. 4
   int flags = 0;
   const float cq = sqrtf(3.f * it.Es / (2.f * float((1 << it.q) - 1)));
+  float rho[NB][2];
+#pragma unroll
+  for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) rho[nt][c] = Gd[nt][c] / it.N0;  // Eq. 13
 #pragma unroll
   for (int hh = 0; hh < 2; ++hh) {
     const int r = g + 8 * hh;
     if (r >= it.R) continue;
     if (cg.broke[hh]) flags |= ST_BREAKDOWN;
-    float mu[NB][2], rho[NB][2], l[NB][2];
+    float mu[NB][2], l[NB][2];
     cg.tracker_l(sAB, hh, l);
 #pragma unroll
     for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        mu[nt][c] = l[nt][c] * Gd[nt][c];          // Eq. 12
-        rho[nt][c] = Gd[nt][c] / it.N0;            // Eq. 13
-      }
+      for (int c = 0; c < 2; ++c) mu[nt][c] = l[nt][c] * Gd[nt][c];  // Eq. 12
     switch (it.q) {
       case 2: store_row_detect<UT, 2, VEC>(it, r, t, cg.v[hh], mu, rho, cq, &flags); break;
       case 4: store_row_detect<UT, 4, VEC>(it, r, t, cg.v[hh], mu, rho, cq, &flags); break;
@@ -596,10 +758,8 @@ __device__ __forceinline__ void detect_warp_instance(const DetItem& it, uint2* f
     }
   }
   flags = __reduce_or_sync(0xffffffffu, flags);
-  if (lane == 0) {
-    if (it.status) *it.status = flags;
-    *status = flags;
-  }
+  if (lane == 0 && it.status) *it.status = flags;
+  return flags;
 }
 
 // Whether an instance may take the vector paths (16-byte loads and stores).
@@ -610,58 +770,95 @@ __device__ __forceinline__ bool detect_vec(const DetItem& it) {
          (it.rho == nullptr || al16(it.rho)) && (it.llr == nullptr || al16(it.llr));
 }
 
+// Claim without waiting: -2 when a serving queue has nothing yet.
+__device__ __forceinline__ int64_t warp_try(const BatchArgs& b) { return warp_claim(b); }
+__device__ __forceinline__ int64_t warp_try(const ServeArgs& s) {
+  int64_t w = -1;
+  if ((threadIdx.x & 31) == 0) w = serve_claim_try(s);
+  return __shfl_sync(0xffffffffu, w, 0);
+}
+
+// Next unit of a warp while it still works on `cur` (-1: none, -2: ask again later).
+template <class S>
+__device__ __forceinline__ int64_t warp_next_early(const S& s, int64_t cur, int64_t nw) {
+  if constexpr (SrcTraits<S>::kDyn) {
+    return warp_try(s);
+  } else {
+    return cur + nw < src_count(s) ? cur + nw : -1;
+  }
+}
+
+// Instance loop: the Gram of an instance, then the next instance's first
+// load stages, then the CG and outputs (which overlap those loads).
 template <int UT, int EL, bool X3, class Src>
 __device__ __forceinline__ void detect_warp_body(const Src& src) {
+  constexpr int NB = UT / 8;
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
   unsigned char* mine = smem + warp * WarpCfg<UT>::WARP_BYTES;
-  uint2* frag = reinterpret_cast<uint2*>(mine);
-  float2* sAB = reinterpret_cast<float2*>(mine + WarpCfg<UT>::FRAG_BYTES);
+  unsigned char* ring = mine;
+  uint2* frag = reinterpret_cast<uint2*>(mine + WarpCfg<UT>::RING_BYTES);
+  float2* sAB = reinterpret_cast<float2*>(mine + WarpCfg<UT>::RING_BYTES + WarpCfg<UT>::FRAG_BYTES);
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
   int64_t cur = warp_first(src, int64_t(blockIdx.x) * (blockDim.x >> 5) + warp);
-  while (cur >= 0) {
+  bool vec = false;
+  if (cur >= 0) {
     const DetItem it = det_item(src, cur);
-    int st = 0;
-    if (detect_vec<UT>(it))
-      detect_warp_instance<UT, EL, X3, true>(it, frag, sAB, &st);
-    else
-      detect_warp_instance<UT, EL, X3, false>(it, frag, sAB, &st);
+    vec = detect_vec<UT>(it);
+    if (vec) ring_gram_prologue<UT, true>(ring, it.H, it.Y, it.B, it.R);
+  }
+  while (cur >= 0) {
+    float Gr[NB][4], Gi[NB][4], Mr[NB][4], Mn[NB][4];
+    {
+      const DetItem it = det_item(src, cur);
+      if (vec)
+        warp_gram<UT, EL, X3, LD_RING, true>(it.H, it.Y, it.B, it.U, it.R, ring, Gr, Gi, Mr, Mn);
+      else
+        warp_gram<UT, EL, X3, LD_ELEM, true>(it.H, it.Y, it.B, it.U, it.R, ring, Gr, Gi, Mr, Mn);
+    }
+    int64_t next = warp_next_early(src, cur, nw);
+    bool nvec = false;
+    if (next >= 0) {
+      const DetItem nit = det_item(src, next);
+      nvec = detect_vec<UT>(nit);
+      if (nvec) ring_gram_prologue<UT, true>(ring, nit.H, nit.Y, nit.B, nit.R);
+    }
+    int st;
+    {
+      const DetItem it = det_item(src, cur);
+      st = vec ? detect_warp_finish<UT, EL, true>(it, frag, sAB, Gr, Gi, Mr, Mn)
+               : detect_warp_finish<UT, EL, false>(it, frag, sAB, Gr, Gi, Mr, Mn);
+    }
     __syncwarp();
     if constexpr (SrcTraits<Src>::kDyn) {
       if ((threadIdx.x & 31) == 0) src_done(src, cur, st);
+      if (next == -2) {  // nothing was ready earlier: wait for work now (bounded)
+        next = warp_claim(src);
+        if (next >= 0) {
+          const DetItem nit = det_item(src, next);
+          nvec = detect_vec<UT>(nit);
+          if (nvec) ring_gram_prologue<UT, true>(ring, nit.H, nit.Y, nit.B, nit.R);
+        }
+      }
     }
-    cur = warp_next(src, cur, nw);
+    cur = next;
+    vec = nvec;
   }
+  cp_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
 // CG-P, one warp per instance
 // ---------------------------------------------------------------------------
 
+// Lines 7-14 with b = t, ||q||, then line 20 (q = H v) of one instance whose
+// Gram is done.
 template <int UT, int EL, bool X3, bool VEC>
-__device__ __forceinline__ void precode_warp_instance(const PreItem& it, uint2* frag, int* status) {
+__device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* frag,
+                                                   const float (&Gr)[UT / 8][4],
+                                                   const float (&Gi)[UT / 8][4]) {
   constexpr int NB = UT / 8;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float Gr[NB][4], Gi[NB][4], Mr[NB][4], Mn[NB][4];
-#pragma unroll
-  for (int nt = 0; nt < NB; ++nt)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) Gr[nt][k] = Gi[nt][k] = Mr[nt][k] = Mn[nt][k] = 0.f;
-
-  // ---- Algorithm 1 line 6: G on the tensor cores
-  const int KS = (it.B + 7) / 8;
-  float2 ha[4], hb[4];
-  const float2 y0[4] = {};
-  load_h_ks<UT, VEC>(it.H, it.B, it.U, 0, g, t, ha);
-  for (int ks = 0; ks < KS; ks += 2) {  // ping-pong: loads run one k-step ahead
-    if (ks + 1 < KS) load_h_ks<UT, VEC>(it.H, it.B, it.U, ks + 1, g, t, hb);
-    gram_ks<UT, EL, X3, false>(ha, y0, Gr, Gi, Mr, Mn);
-    if (ks + 1 >= KS) break;
-    if (ks + 2 < KS) load_h_ks<UT, VEC>(it.H, it.B, it.U, ks + 2, g, t, ha);
-    gram_ks<UT, EL, X3, false>(hb, y0, Gr, Gi, Mr, Mn);
-  }
-
-  // ---- lines 7-14 with b = t
   WarpCg<UT, EL> cg;
   float Gd[NB][2];
   WarpCg<UT, EL>::setup_a(Gr, Gi, it.sigma, frag, cg.D, Gd);
@@ -728,24 +925,26 @@ __device__ __forceinline__ void precode_warp_instance(const PreItem& it, uint2* 
     vh[ks][2] = s2.x; vl[ks][2] = s2.y;
     vh[ks][3] = s3.x; vl[ks][3] = s3.y;
   }
+  // H is read a second time here (L1 or L2: the Gram read it moments ago);
+  // VEC keeps the 16-byte loads of the next n-tile in flight.
   const int NBQ = (it.B + 7) / 8;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 fa0 = zero4, fa1 = zero4;
+  if constexpr (VEC) q_load<UT>(it.H, it.B, 0, g, t, fa0, fa1);
   for (int nb = 0; nb < NBQ; ++nb) {
     const int b = 8 * nb + g;
     // lane's H entries at its k-positions: e[ks][j] = H(b, user(8 ks + 2 t + j))
     float2 e[NB][2];
     const float2 z = make_float2(0.f, 0.f);
     if constexpr (VEC) {
-      const bool ok = b < it.B;
+      const float4 f0 = fa0, f1 = fa1;
+      if (nb + 1 < NBQ) q_load<UT>(it.H, it.B, nb + 1, g, t, fa0, fa1);
       if constexpr (UT == 16) {
-        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 f0 = ok ? ldg4(it.H + b * 16 + 4 * t) : zero4;      // users 4t, 4t+1
-        const float4 f1 = ok ? ldg4(it.H + b * 16 + 4 * t + 2) : zero4;  // users 4t+2, 4t+3
-        e[0][0] = make_float2(f0.x, f0.y);
-        e[1][0] = make_float2(f0.z, f0.w);
-        e[0][1] = make_float2(f1.x, f1.y);
-        e[1][1] = make_float2(f1.z, f1.w);
+        e[0][0] = make_float2(f0.x, f0.y);  // user 4t
+        e[1][0] = make_float2(f0.z, f0.w);  // user 4t + 1
+        e[0][1] = make_float2(f1.x, f1.y);  // user 4t + 2
+        e[1][1] = make_float2(f1.z, f1.w);  // user 4t + 3
       } else {
-        const float4 f0 = ok ? ldg4(it.H + b * 8 + 2 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
         e[0][0] = make_float2(f0.x, f0.y);
         e[0][1] = make_float2(f0.z, f0.w);
       }
@@ -786,10 +985,8 @@ __device__ __forceinline__ void precode_warp_instance(const PreItem& it, uint2* 
     }
   }
   flags = __reduce_or_sync(0xffffffffu, flags);
-  if (lane == 0) {
-    if (it.status) *it.status = flags;
-    *status = flags;
-  }
+  if (lane == 0 && it.status) *it.status = flags;
+  return flags;
 }
 
 // Whether an instance may take the vector paths.
@@ -798,25 +995,36 @@ __device__ __forceinline__ bool precode_vec(const PreItem& it) {
   return it.U == UT && (it.B % 2) == 0 && al16(it.H) && al16(it.q);
 }
 
+// Instance loop. CG-P reads H twice (Gram, then q = H v); both passes use
+// 16-byte register loads through L1, where the second pass finds part of H.
 template <int UT, int EL, bool X3, class Src>
 __device__ __forceinline__ void precode_warp_body(const Src& src) {
+  constexpr int NB = UT / 8;
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
-  uint2* frag = reinterpret_cast<uint2*>(smem + warp * WarpCfg<UT>::WARP_BYTES);
+  uint2* frag = reinterpret_cast<uint2*>(smem + warp * WarpCfg<UT>::FRAG_BYTES);
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
   int64_t cur = warp_first(src, int64_t(blockIdx.x) * (blockDim.x >> 5) + warp);
   while (cur >= 0) {
     const PreItem it = pre_item(src, cur);
-    int st = 0;
-    if (precode_vec<UT>(it))
-      precode_warp_instance<UT, EL, X3, true>(it, frag, &st);
-    else
-      precode_warp_instance<UT, EL, X3, false>(it, frag, &st);
+    float Gr[NB][4], Gi[NB][4], Mr[NB][4], Mn[NB][4];
+    int st;
+    if (precode_vec<UT>(it)) {
+      warp_gram<UT, EL, X3, LD_VEC, false>(it.H, nullptr, it.B, it.U, 0, nullptr, Gr, Gi, Mr, Mn);
+      st = precode_warp_finish<UT, EL, X3, true>(it, frag, Gr, Gi);
+    } else {
+      warp_gram<UT, EL, X3, LD_ELEM, false>(it.H, nullptr, it.B, it.U, 0, nullptr, Gr, Gi, Mr,
+                                            Mn);
+      st = precode_warp_finish<UT, EL, X3, false>(it, frag, Gr, Gi);
+    }
     __syncwarp();
     if constexpr (SrcTraits<Src>::kDyn) {
       if ((threadIdx.x & 31) == 0) src_done(src, cur, st);
     }
-    cur = warp_next(src, cur, nw);
+    cur = warp_next_early(src, cur, nw);
+    if constexpr (SrcTraits<Src>::kDyn) {
+      if (cur == -2) cur = warp_claim(src);
+    }
   }
 }
 
@@ -839,12 +1047,16 @@ __global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB)
 }
 template <int UT, int EL, bool X3>
 __global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB) detect_warp_serve_kernel(const ServeArgs s) {
+  if ((threadIdx.x & 31) == 0) serve_unit_enter(s);
   detect_warp_body<UT, EL, X3>(s);
+  if ((threadIdx.x & 31) == 0) serve_unit_exit(s);
 }
 template <int UT, int EL, bool X3>
 __global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB)
     precode_warp_serve_kernel(const ServeArgs s) {
+  if ((threadIdx.x & 31) == 0) serve_unit_enter(s);
   precode_warp_body<UT, EL, X3>(s);
+  if ((threadIdx.x & 31) == 0) serve_unit_exit(s);
 }
 
 }  // namespace cgm

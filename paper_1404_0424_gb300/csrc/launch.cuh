@@ -52,6 +52,18 @@ cudaError_t launch_batch_warp(int op, int UT, int el, bool x3, const BatchArgs& 
 cudaError_t launch_serve_warp(int op, int UT, int el, bool x3, const ServeArgs& sa, int grid,
                               cudaStream_t s, bool launch, int* resident_out);
 
+// Implicit-product FP32 kernels (implicit.cu): e = H^H (H p) + sigma p.
+cudaError_t launch_detect_implicit(int UT, const DetectArgs& a, cudaStream_t s);
+cudaError_t launch_precode_implicit(int UT, const PrecodeArgs& a, cudaStream_t s);
+
+// Whether A p is applied implicitly for these parameters: requested, or
+// CG_AMUL_AUTO on the FP32 path when the two products per iteration cost
+// fewer complex multiply-adds than the Gram (4 K R < U + 1).
+inline bool use_implicit(int amul_mode, int precision, int K, int R, int U, bool exact) {
+  if (amul_mode == 2) return true;  // CG_AMUL_IMPLICIT
+  return amul_mode == 0 && precision == 0 && !exact && 4 * K * R < U + 1;
+}
+
 // Dynamic shared memory of one CTA for the given shape (bytes).
 uint32_t detect_smem_bytes(int UT, int B, int U, int R, int exact);
 uint32_t precode_smem_bytes(int UT, int B, int U, int R);

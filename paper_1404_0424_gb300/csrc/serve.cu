@@ -1,6 +1,7 @@
 // Host side of the serving loop behind cg_serve_*: ring slots, admission by
-// HBM budget, publication through mapped host memory, on-demand launch of
-// the persistent class kernels, completion polling and bounded shutdown.
+// HBM budget, stream-ordered publication into device memory (no host wait),
+// on-demand launch of the persistent class kernels (liveness read from
+// mapped memory, no CUDA call), completion polling and bounded shutdown.
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -58,19 +59,26 @@ struct cg_server {
   cg_serve_cfg cfg{};
   int el = 1;
   bool x3 = true;
+  // device memory: slot records, class heads, class tails, class rings
   void* dmem = nullptr;
   ServeSlot* d_slots = nullptr;
   unsigned long long* d_head = nullptr;
+  unsigned long long* d_tail = nullptr;
+  unsigned long long* d_ring = nullptr;
+  // pinned staging of the asynchronous copies that publish a request
+  void* smem_host = nullptr;
+  ServeSlot* st_slot = nullptr;          // [cap] slot records
+  unsigned long long* st_ring = nullptr;  // [classes][cap] ring entries
+  unsigned long long* st_tail = nullptr;  // [cap] class tail published with each ticket
+  // mapped host memory: control block and completion records
   void* hmem = nullptr;
-  unsigned long long* h_ring = nullptr;
   ServeCtrl* h_ctrl = nullptr;
   ServeCompletion* h_comp = nullptr;
-  unsigned long long* d_ring = nullptr;
   ServeCtrl* d_ctrl = nullptr;
   ServeCompletion* d_comp = nullptr;
   cudaStream_t ks[kClasses] = {};
   cudaStream_t cs = nullptr;
-  bool launched[kClasses] = {};
+  unsigned long long launched_gen[kClasses] = {};
   int grid[kClasses] = {};
   std::mutex mu;
   uint64_t next = 0, head = 0;
@@ -85,6 +93,7 @@ ServeArgs args_for(const cg_server* s, int cls) {
   ServeArgs a{};
   a.slots = s->d_slots;
   a.class_ring = s->d_ring;
+  a.class_tail = s->d_tail;
   a.ctrl = s->d_ctrl;
   a.comp = s->d_comp;
   a.class_head = s->d_head;
@@ -94,23 +103,27 @@ ServeArgs args_for(const cg_server* s, int cls) {
   a.PR = s->cfg.max_R;
   a.PEX = cls == 2 ? 1 : 0;
   a.idle_ns = (unsigned long long)s->cfg.idle_timeout_ms * 1000000ull;
+  a.gen = s->launched_gen[cls];
   return a;
 }
 
 int class_ut(int cls) { return cls % 3 == 0 ? 8 : cls % 3 == 1 ? 16 : 32; }
 
-// Launches the class kernel if it is not running (never launched, or its
-// previous launch has exited on the idle timeout).
+// Launches the class kernel unless a launch of it is still alive: the last
+// work unit of launch generation g to exit writes g into the mapped control
+// block, so the check is a memory read. A relaunch queues on the class
+// stream behind a launch that is just finishing.
 int ensure_running(cg_server* s, int cls) {
-  if (s->launched[cls]) {
-    const cudaError_t q = cudaStreamQuery(s->ks[cls]);
-    if (q == cudaErrorNotReady) return CG_OK;
-    if (q != cudaSuccess) return CG_ECUDA;
-  }
+  const auto* ex = reinterpret_cast<const std::atomic<unsigned long long>*>(
+      &s->h_ctrl->exited_gen[cls]);
+  if (s->launched_gen[cls] > ex->load(std::memory_order_acquire)) return CG_OK;
+  ++s->launched_gen[cls];
   const cudaError_t err = launch_serve_tc(cls / 3, class_ut(cls), s->el, s->x3, args_for(s, cls),
                                           s->grid[cls], s->ks[cls], true, nullptr, nullptr);
-  if (err != cudaSuccess) return CG_ECUDA;
-  s->launched[cls] = true;
+  if (err != cudaSuccess) {
+    --s->launched_gen[cls];
+    return CG_ECUDA;
+  }
   return CG_OK;
 }
 
@@ -140,6 +153,7 @@ void destroy_server(cg_server* s) {
   if (s->cs) cudaStreamDestroy(s->cs);
   if (s->dmem) cudaFree(s->dmem);
   if (s->hmem) cudaFreeHost(s->hmem);
+  if (s->smem_host) cudaFreeHost(s->smem_host);
   delete s;
 }
 
@@ -167,11 +181,16 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
     return CG_ECUDA;
   }
   const size_t cap = size_t(c.capacity);
-  const size_t dbytes = sizeof(ServeSlot) * cap + sizeof(unsigned long long) * 8;
-  const size_t ring_bytes = (sizeof(unsigned long long) * kClasses * cap + 255) & ~size_t(255);
-  const size_t ctrl_off = ring_bytes;
-  const size_t comp_off = (ctrl_off + sizeof(ServeCtrl) + 255) & ~size_t(255);
+  const size_t u64 = sizeof(unsigned long long);
+  const size_t head_off = sizeof(ServeSlot) * cap;
+  const size_t tail_off = head_off + u64 * 8;
+  const size_t ring_off = tail_off + u64 * 8;
+  const size_t dbytes = ring_off + u64 * kClasses * cap;
+  const size_t comp_off = (sizeof(ServeCtrl) + 255) & ~size_t(255);
   const size_t hbytes = comp_off + sizeof(ServeCompletion) * cap;
+  const size_t st_ring_off = sizeof(ServeSlot) * cap;
+  const size_t st_tail_off = st_ring_off + u64 * kClasses * cap;
+  const size_t sbytes = st_tail_off + u64 * cap;
   int rc = CG_OK;
   if (cudaMalloc(&s->dmem, dbytes) != cudaSuccess) {
     s->dmem = nullptr;
@@ -181,19 +200,29 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
     s->hmem = nullptr;
     rc = CG_ENOMEM;
   }
+  if (rc == CG_OK && cudaHostAlloc(&s->smem_host, sbytes, cudaHostAllocDefault) != cudaSuccess) {
+    s->smem_host = nullptr;
+    rc = CG_ENOMEM;
+  }
   if (rc == CG_OK) {
     std::memset(s->hmem, 0, hbytes);
-    s->d_slots = static_cast<ServeSlot*>(s->dmem);
-    s->d_head = reinterpret_cast<unsigned long long*>(s->d_slots + cap);
+    std::memset(s->smem_host, 0, sbytes);
+    char* dm = static_cast<char*>(s->dmem);
+    s->d_slots = reinterpret_cast<ServeSlot*>(dm);
+    s->d_head = reinterpret_cast<unsigned long long*>(dm + head_off);
+    s->d_tail = reinterpret_cast<unsigned long long*>(dm + tail_off);
+    s->d_ring = reinterpret_cast<unsigned long long*>(dm + ring_off);
+    char* st = static_cast<char*>(s->smem_host);
+    s->st_slot = reinterpret_cast<ServeSlot*>(st);
+    s->st_ring = reinterpret_cast<unsigned long long*>(st + st_ring_off);
+    s->st_tail = reinterpret_cast<unsigned long long*>(st + st_tail_off);
     char* h = static_cast<char*>(s->hmem);
-    s->h_ring = reinterpret_cast<unsigned long long*>(h);
-    s->h_ctrl = reinterpret_cast<ServeCtrl*>(h + ctrl_off);
+    s->h_ctrl = reinterpret_cast<ServeCtrl*>(h);
     s->h_comp = reinterpret_cast<ServeCompletion*>(h + comp_off);
     void* dv = nullptr;
     if (cudaHostGetDevicePointer(&dv, s->hmem, 0) != cudaSuccess) rc = CG_ECUDA;
     char* d = static_cast<char*>(dv);
-    s->d_ring = reinterpret_cast<unsigned long long*>(d);
-    s->d_ctrl = reinterpret_cast<ServeCtrl*>(d + ctrl_off);
+    s->d_ctrl = reinterpret_cast<ServeCtrl*>(d);
     s->d_comp = reinterpret_cast<ServeCompletion*>(d + comp_off);
   }
   if (rc == CG_OK && cudaMemset(s->dmem, 0, dbytes) != cudaSuccess) rc = CG_ECUDA;
@@ -201,9 +230,13 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
     if (cudaStreamCreateWithFlags(&s->ks[k], cudaStreamNonBlocking) != cudaSuccess) rc = CG_ECUDA;
   if (rc == CG_OK && cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess)
     rc = CG_ECUDA;
-  // launch shapes: an equal share of each class kernel's resident CTAs
+  // launch shapes: each class gets a share of the SMs in proportion to the
+  // cost of one of its instances (weights 1, 2, 8 for 8, 16, 32 padded
+  // users), as many work units as are resident on that share
   DeviceInfo di;
   if (rc == CG_OK && device_info(&di) != 0) rc = CG_ECUDA;
+  const double weight[3] = {1.0, 2.0, 8.0};
+  const double wsum = 2.0 * (weight[0] + weight[1] + weight[2]);
   for (int k = 0; k < kClasses && rc == CG_OK; ++k) {
     uint32_t smem = 0;
     int resident = 0;
@@ -213,7 +246,7 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
       rc = err == cudaErrorInvalidValue ? CG_EINVAL : CG_ECUDA;
       break;
     }
-    const int share = resident / kClasses;
+    const int share = int(double(resident) * weight[k % 3] / wsum + 0.5);
     s->grid[k] = c.ctas_per_class > 0 ? c.ctas_per_class : (share > 0 ? share : 1);
   }
   if (rc != CG_OK) {
@@ -262,21 +295,28 @@ int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket) {
   const uint64_t t = s->next;
   const uint64_t slot = t % cap;
   if (t >> (64 - SERVE_NINST_BITS)) return CG_ETOOBIG;  // ticket space exhausted
-  ServeSlot rec{};
+  // publication: the slot record, the class ring entry and the new class
+  // tail are copied in that order on one stream, so the device sees the
+  // tail only after the record and the entry have landed. Each copy reads
+  // its own pinned staging word (records and tails per slot, entries per
+  // ring position), which stays unchanged until the copy has run.
+  ServeSlot& rec = s->st_slot[slot];
+  rec = ServeSlot{};
   rec.d = d;
   rec.ticket = t;
   rec.claim = (t & 0xffffffffull) << 32;
   std::memset(&s->h_comp[slot], 0, sizeof(ServeCompletion));
+  const size_t pos = size_t(cls) * cap + size_t(s->published[cls] % cap);
+  s->st_ring[pos] = (t << SERVE_NINST_BITS) | uint64_t(d.n_inst);
+  s->st_tail[slot] = s->published[cls] + 1;
   if (cudaMemcpyAsync(s->d_slots + slot, &rec, sizeof(rec), cudaMemcpyHostToDevice, s->cs) !=
           cudaSuccess ||
-      cudaStreamSynchronize(s->cs) != cudaSuccess)
+      cudaMemcpyAsync(s->d_ring + pos, &s->st_ring[pos], sizeof(unsigned long long),
+                      cudaMemcpyHostToDevice, s->cs) != cudaSuccess ||
+      cudaMemcpyAsync(s->d_tail + cls, &s->st_tail[slot], sizeof(unsigned long long),
+                      cudaMemcpyHostToDevice, s->cs) != cudaSuccess)
     return CG_ECUDA;
-  reinterpret_cast<std::atomic<unsigned long long>*>(
-      &s->h_ring[cls * s->cfg.capacity + int(s->published[cls] % cap)])
-      ->store((t << SERVE_NINST_BITS) | uint64_t(d.n_inst), std::memory_order_relaxed);
   ++s->published[cls];
-  reinterpret_cast<std::atomic<unsigned long long>*>(&s->h_ctrl->class_tail[cls])
-      ->store(s->published[cls], std::memory_order_release);
   SlotInfo& in = s->info[slot];
   in.ticket = t;
   in.cls = cls;
@@ -326,13 +366,14 @@ int cg_serve_destroy(cg_server* s) {
   }
   const auto t0 = std::chrono::steady_clock::now();
   for (int k = 0; k < kClasses; ++k) {
-    while (s->launched[k]) {
+    while (s->launched_gen[k] > 0) {
       const cudaError_t q = cudaStreamQuery(s->ks[k]);
       if (q != cudaErrorNotReady) break;
       if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(10)) return CG_ETIMEDOUT;
       std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
   }
+  if (cudaStreamSynchronize(s->cs) != cudaSuccess) return CG_ECUDA;
   destroy_server(s);
   return CG_OK;
 }

@@ -26,6 +26,9 @@ cudaError_t resident_ctas(Kern kern, uint64_t id, uint32_t smem, int* out) {
   auto it = g_occ.find(key);
   int occ = 0;
   if (it == g_occ.end()) {
+    if (int(smem) > di.smem_optin) return cudaErrorInvalidValue;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (err != cudaSuccess) return err;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem);
     if (err != cudaSuccess) return err;
     if (occ < 1) occ = 1;
@@ -59,7 +62,7 @@ cudaError_t det(const DetectArgs& a, cudaStream_t s) {
 
 template <int UT, int EL, bool X3>
 cudaError_t pre(const PrecodeArgs& a, cudaStream_t s) {
-  constexpr uint32_t smem = WarpCfg<UT>::SMEM;
+  constexpr uint32_t smem = WarpCfg<UT>::PRE_SMEM;
   int res = 0;
   const uint64_t id = 0x200 | (UT << 2) | (EL << 1) | (X3 ? 1 : 0);
   cudaError_t err = resident_ctas(precode_warp_kernel<UT, EL, X3>, id, smem, &res);
@@ -72,7 +75,7 @@ cudaError_t pre(const PrecodeArgs& a, cudaStream_t s) {
 template <int UT, int EL, bool X3>
 cudaError_t batch(int op, const BatchArgs& b, int max_grid, cudaStream_t s, bool launch,
                   int* grid_out) {
-  constexpr uint32_t smem = WarpCfg<UT>::SMEM;
+  const uint32_t smem = op == 0 ? WarpCfg<UT>::SMEM : WarpCfg<UT>::PRE_SMEM;
   int res = 0;
   const uint64_t id = (op == 0 ? 0x400 : 0x800) | (UT << 2) | (EL << 1) | (X3 ? 1 : 0);
   cudaError_t err = op == 0 ? resident_ctas(detect_warp_batch_kernel<UT, EL, X3>, id, smem, &res)
@@ -91,7 +94,7 @@ cudaError_t batch(int op, const BatchArgs& b, int max_grid, cudaStream_t s, bool
 template <int UT, int EL, bool X3>
 cudaError_t serve(int op, const ServeArgs& sa, int grid, cudaStream_t s, bool launch,
                   int* resident_out) {
-  constexpr uint32_t smem = WarpCfg<UT>::SMEM;
+  const uint32_t smem = op == 0 ? WarpCfg<UT>::SMEM : WarpCfg<UT>::PRE_SMEM;
   int res = 0;
   const uint64_t id = (op == 0 ? 0x1000 : 0x2000) | (UT << 2) | (EL << 1) | (X3 ? 1 : 0);
   cudaError_t err = op == 0 ? resident_ctas(detect_warp_serve_kernel<UT, EL, X3>, id, smem, &res)

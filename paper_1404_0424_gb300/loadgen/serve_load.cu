@@ -158,6 +158,10 @@ int main(int argc, char** argv) {
   std::vector<int> free_regions;
   for (int k = capacity - 1; k >= 0; --k) free_regions.push_back(k);
   std::vector<double> lat_ms;
+  std::vector<double> cls_lat[6];  // (operation, padded users 8 / 16 / 32)
+  auto cls_of = [](const cg_desc& d) {
+    return d.op * 3 + (d.U <= 8 ? 0 : d.U <= 16 ? 1 : 2);
+  };
   int64_t solves_done = 0, eagain = 0;
   size_t next = 0, max_inflight = 0;
   const int64_t t0 = now_ns();
@@ -214,7 +218,9 @@ int main(int argc, char** argv) {
         if (rc == CG_OK) rc = cudaEventRecord(evs[size_t(region)], st) == cudaSuccess ? CG_OK : CG_ECUDA;
       }
       if (rc != CG_OK) {
-        printf("{\"error\": \"submit: %s\"}\n", cg_strerror(rc));
+        printf("{\"error\": \"submit: %s\", \"op\": %d, \"B\": %d, \"U\": %d, \"R\": %d, "
+               "\"K\": %d, \"n\": %lld}\n",
+               cg_strerror(rc), r.d.op, r.d.B, r.d.U, r.d.R, r.d.K, (long long)r.d.n_inst);
         return 1;
       }
       free_regions.pop_back();
@@ -240,6 +246,7 @@ int main(int argc, char** argv) {
       if (done) {
         const int64_t tdone = now_ns();
         lat_ms.push_back(double(tdone - t0 - reqs[f.req].arrival_ns) * 1e-6);
+        cls_lat[cls_of(reqs[f.req].d)].push_back(lat_ms.back());
         solves_done += reqs[f.req].solves;
         last_done = tdone;
         free_regions.push_back(f.region);
@@ -258,13 +265,22 @@ int main(int argc, char** argv) {
   double mean = 0;
   for (double v : lat_ms) mean += v;
   mean = lat_ms.empty() ? 0 : mean / lat_ms.size();
+  std::string per_class = "{";
+  const char* names[6] = {"detect8", "detect16", "detect32", "precode8", "precode16", "precode32"};
+  for (int c = 0; c < 6; ++c) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "%s\"%s\": [%zu, %.4f, %.4f]", c ? ", " : "", names[c],
+             cls_lat[c].size(), pct(cls_lat[c], 0.5), pct(cls_lat[c], 0.99));
+    per_class += buf;
+  }
+  per_class += "}";
   printf("{\"mode\": \"%s\", \"requests\": %zu, \"completed\": %zu, \"offered_rps\": %.1f, "
          "\"achieved_rps\": %.1f, \"solves_per_s\": %.1f, \"lat_p50_ms\": %.4f, "
          "\"lat_p99_ms\": %.4f, \"lat_mean_ms\": %.4f, \"max_inflight\": %zu, \"eagain\": %lld, "
-         "\"precision\": %d}\n",
+         "\"precision\": %d, \"per_class_count_p50_p99_ms\": %s}\n",
          mode.c_str(), reqs.size(), lat_ms.size(), reqs.size() / seconds,
          lat_ms.size() / std::max(elapsed, 1e-9), solves_done / std::max(elapsed, 1e-9),
          pct(lat_ms, 0.5), pct(lat_ms, 0.99), mean, max_inflight, (long long)eagain,
-         served ? precision : 0);
+         served ? precision : 0, per_class.c_str());
   return lat_ms.size() == reqs.size() ? 0 : 2;
 }

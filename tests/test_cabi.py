@@ -67,6 +67,9 @@ def test_detect_rejects_bad_modes_pointers_and_counts(lib):
     assert cabi.cg_detect(p, 1, 16, 16) == cabi.CG_EINVAL
     p = cabi.params(32, 4, 4, 3, 1, 0.4, precision=9)
     assert cabi.cg_detect(p, 1, 16, 16) == cabi.CG_EINVAL
+    # the exact tracker needs the Gram: no implicit product with it
+    p = cabi.params(32, 4, 4, 3, 1, 0.4, sinr_mode=1, amul_mode=2)
+    assert cabi.cg_detect(p, 1, 16, 16) == cabi.CG_ENOTSUP
     p = cabi.params(32, 4, 4, 3, 1, 0.4, Es=0.0)
     assert cabi.cg_detect(p, 1, 16, 16) == cabi.CG_EINVAL
     p = cabi.params(**GOOD)

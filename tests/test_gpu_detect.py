@@ -171,3 +171,32 @@ def test_host_variant_matches_device(cabi):
     assert rc == 0, cabi.cg_strerror(rc)
     assert np.array_equal(xh, g["xhat"]) and np.array_equal(llr, g["llr"])
     assert np.array_equal(mu, g["mu"]) and np.array_equal(st, g["status"])
+
+
+@pytest.mark.parametrize("B,U,R,K,q", [
+    (128, 16, 14, 3, 6), (128, 8, 14, 2, 6), (128, 16, 1, 1, 6), (32, 4, 1, 3, 4),
+    (256, 32, 2, 4, 8), (33, 7, 5, 3, 6), (1, 1, 1, 1, 2), (64, 13, 16, 5, 4)])
+def test_implicit_product_matches_oracle(cabi, B, U, R, K, q):
+    # e = H^H (H p) + sigma p without forming the Gram (CG_AMUL_IMPLICIT)
+    d = wl.uplink(B, U, q, n=4, R=R, snr_db=10.0, seed=7000 + B + U + R + K)
+    check_detect(run(cabi, d, K, amul_mode=2), ref(d, K))
+
+
+def test_auto_picks_the_product_by_cost_and_both_agree(cabi):
+    # 4 K R < U + 1: AUTO applies A p implicitly on the FP32 path
+    d = wl.uplink(128, 16, 6, n=6, R=1, snr_db=10.0, seed=71)
+    auto = run(cabi, d, 2)
+    expl = run(cabi, d, 2, amul_mode=1)
+    impl = run(cabi, d, 2, amul_mode=2)
+    for k in auto:
+        assert np.array_equal(auto[k], impl[k]), k
+    check_detect(expl, ref(d, 2))
+    check_detect(impl, ref(d, 2))
+    err = np.abs(impl["xhat"] - expl["xhat"]).max() / np.abs(expl["xhat"]).max()
+    assert err < 1e-5
+
+
+def test_implicit_product_with_exact_tracker_is_not_supported(cabi):
+    d = wl.uplink(32, 4, 4, n=2, R=1, snr_db=10.0, seed=72)
+    with pytest.raises(cabi.CgError):
+        run(cabi, d, 2, tracker="exact", amul_mode=2)

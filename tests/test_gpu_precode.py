@@ -112,3 +112,16 @@ def test_host_variant_matches_device(cabi):
     rc = cabi.cg_precode_host(p, 200, d["H"], d["T"], q, qn, 0, st)
     assert rc == 0, cabi.cg_strerror(rc)
     assert np.array_equal(q, g["q"]) and np.array_equal(qn, g["qnorm"])
+
+
+@pytest.mark.parametrize("B,U,R,K", [(128, 16, 14, 3), (128, 8, 1, 1), (256, 32, 3, 4),
+                                     (33, 7, 5, 3), (1, 1, 1, 1)])
+@pytest.mark.parametrize("normalize", [False, True])
+def test_implicit_product_matches_oracle(cabi, B, U, R, K, normalize):
+    d = wl.downlink(B, U, 6, n=4, R=R, snr_db=10.0, seed=8000 + B + U + R + K)
+    dev = torch.device("cuda:0")
+    out = cabi.precode(torch.from_numpy(d["H"]).to(dev), torch.from_numpy(d["T"]).to(dev),
+                       d["N0"], K, d["Es"], normalize=normalize, amul_mode=2)
+    torch.cuda.synchronize()
+    check_precode({k: to_np(v) for k, v in out.items()},
+                  oracle.cg_precode(d["H"], d["T"], d["N0"], d["Es"], K), normalize=normalize)

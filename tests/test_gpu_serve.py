@@ -90,6 +90,9 @@ def as_desc(cabi, r, o):
 
 
 def submit(cabi, srv, d, timeout=20.0):
+    # the request's buffers must be ready when it is submitted: the serving
+    # kernels run on their own streams and do not wait for torch's stream
+    torch.cuda.current_stream().synchronize()
     t0 = time.monotonic()
     while True:
         rc, t = cabi.cg_serve_submit(srv, d)
@@ -151,6 +154,7 @@ def test_admission_by_slots_and_budget(cabi):
     assert rc == 0
     try:
         o1, o2 = fresh_outputs(r, dev), fresh_outputs(r, dev)
+        torch.cuda.current_stream().synchronize()
         rc, t1 = cabi.cg_serve_submit(srv, as_desc(cabi, r, o1))
         assert rc == 0
         rc, _ = cabi.cg_serve_submit(srv, as_desc(cabi, r, o2))
@@ -169,6 +173,7 @@ def test_admission_by_slots_and_budget(cabi):
     rc, srv = cabi.cg_serve_create(capacity=1, precision=4, idle_timeout_ms=300)
     try:
         o1, o2 = fresh_outputs(r, dev), fresh_outputs(r, dev)
+        torch.cuda.current_stream().synchronize()
         rc, t1 = cabi.cg_serve_submit(srv, as_desc(cabi, r, o1))
         assert rc == 0
         rc2, _ = cabi.cg_serve_submit(srv, as_desc(cabi, r, o2))
@@ -213,6 +218,7 @@ def test_slots_are_reused_only_after_poll_and_results_hold_under_reuse(cabi):
         r["H"] = r["H"][:r["n"]].contiguous()
         r["inp"] = r["inp"][:r["n"]].contiguous()
     outs = [fresh_outputs(r, dev) for r in reqs]
+    torch.cuda.current_stream().synchronize()
     rc, srv = cabi.cg_serve_create(capacity=4, precision=4, idle_timeout_ms=300)
     assert rc == 0, cabi.cg_strerror(rc)
     try:
