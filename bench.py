@@ -125,6 +125,16 @@ def precode_bytes_per_instance(Bn, Un, Rn):
     return (Bn * Un + Rn * Un) * 8 + Rn * Bn * 8 + Rn * 4 + 4
 
 
+def detect_kernel_name(precision: str, Un: int) -> str:
+    """The detection kernel the C ABI dispatches to for this precision."""
+    if precision == "fp32":
+        return f"detect_kernel<{Un}>"
+    el = "BF16" if precision.startswith("bf16") else "FP16"
+    x3 = "true" if precision.endswith("x3") else "false"
+    ut = 8 if Un <= 8 else 16 if Un <= 16 else 32
+    return f"detect_warp_kernel<{ut}, {el}, {x3}>"
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1404_0424_gb300", "csrc")
@@ -446,7 +456,8 @@ def run_ours(args):
     traffic = profiled_traffic(f"detect_{args.precision}_{B}x{Un}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "traffic": traffic, "kernel": "detect_kernel", "peak_kind": peak_kind,
+                "traffic": traffic, "kernel": detect_kernel_name(args.precision, Un),
+                "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": det_bytes}
     pre_bytes = precode_bytes_per_instance(B, Un, R) * n
     pre_gbs = pre_bytes / (pre_ms / 1e3) / 1e9

@@ -204,15 +204,16 @@ int cg_plan_destroy(cg_plan* plan);
  * ------------------------------------------------------------------------ */
 
 /* Server configuration.
- *   capacity          requests in flight at most (ring slots), >= 1
+ *   capacity          requests in flight at most (ring slots), 1 to 16384
  *   precision         CG_PREC_BF16, CG_PREC_FP16, CG_PREC_BF16X3 or CG_PREC_FP16X3
  *   hbm_budget_bytes  admission limit: input + output bytes of admitted,
  *                     unfinished requests (a request larger than it is CG_ETOOBIG)
  *   max_B, max_R      largest B and R a request may have (they size the kernels)
- *   ctas_per_class    persistent work units (CTAs) of each class kernel; 0 = a
- *                     share of the SMs per class in proportion to the cost of
- *                     one of its instances (weights 1, 2, 8 for 8, 16 and 32
- *                     padded users, for each operation)
+ *   ctas_per_class    upper limit on the CTAs of each serving kernel; 0 = no
+ *                     limit. Every serving CTA fills one SM: the kernel for the
+ *                     approximate tracker holds all SMs but 1/16, which the
+ *                     exact-tracker kernel holds, so either one always finds
+ *                     room when it is relaunched
  *   idle_timeout_ms   a class kernel exits after this long without work and is
  *                     relaunched by the next submit or poll that needs it          */
 typedef struct cg_serve_cfg {
@@ -237,13 +238,17 @@ typedef struct cg_req_stats {
 
 typedef struct cg_server cg_server;
 
-/* Creates a server on the current device and starts nothing yet: the class
- * kernels (detection or precoding x padded user count 8, 16, 32) launch on
- * the first request of their class, each on its own stream. Requests are
- * published through pinned, mapped host memory; a request's instances are
- * claimed one at a time by any CTA of its class, oldest request first, so
- * requests that arrive while others run are admitted as CTAs free up and
- * their work overlaps on the device. Every device wait is bounded. */
+/* Creates a server on the current device and starts nothing yet. Requests
+ * fall into classes by operation and padded user count (8, 16, 32), plus one
+ * for exact-tracker detection, each published in order through its own ring
+ * in pinned, mapped host memory. One persistent kernel serves the six
+ * approximate-tracker classes: each of its warps takes instances of the
+ * oldest request of its home class while there are any, and otherwise of
+ * another class that has work, so a request alone on the device is spread
+ * over every SM, and requests that arrive while others run are admitted as
+ * warps free up. A second kernel serves the exact class. Each kernel
+ * launches on the first request that needs it, on its own stream, and exits
+ * after idle_timeout_ms without work. Every device wait is bounded. */
 int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out);
 
 /* Non-blocking submit of one request (a cg_desc with 1 <= n_inst < 2^24
@@ -252,8 +257,9 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out);
  * and retry), CG_EINVAL for an invalid request, CG_ETOOBIG when it alone
  * exceeds the budget or has 2^24 instances or more; on success *ticket
  * identifies it. A request's bytes count against the budget until it
- * completes; its ring slot stays in use until a cg_serve_poll has reported
- * it done, so poll every ticket until done. Slots are freed in ticket order.
+ * completes; its slot stays in use until a cg_serve_poll has reported it
+ * done, so poll every ticket until done. Submitting makes no CUDA call: the
+ * request is published through pinned, mapped host memory.
  * The server's kernels run on streams of their own and may start on the
  * request at once: its inputs must already hold their values, and no other
  * work may touch its outputs, when submit is called (synchronise the stream
@@ -264,7 +270,8 @@ int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket);
  * are visible to the host; stats (may be NULL) are filled when done. The
  * first poll that reports done releases the ticket's slot; later polls of
  * the same ticket report done again until the slot is reused by a newer
- * request, after which they return CG_EINVAL. */
+ * request, after which they return CG_EINVAL. Polling makes no CUDA call
+ * unless the request's class kernel has exited and must be relaunched. */
 int cg_serve_poll(cg_server* s, uint64_t ticket, int32_t* done, cg_req_stats* stats);
 
 /* Stops the class kernels (bounded wait) and frees the server. Requests still

@@ -28,6 +28,12 @@ int device_info(DeviceInfo* out) {
     if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
         cudaSuccess)
       return -1;
+    if (cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+        cudaSuccess)
+      return -1;
+    if (cudaDeviceGetAttribute(&d.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+        cudaSuccess)
+      return -1;
     g_dev[dev] = d;
     g_dev_ok[dev] = true;
   }
@@ -85,7 +91,7 @@ int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void*
     bool x3;
     tc_mode(p->precision, &el, &x3);
     const int UT = padded_users(p->U);
-    if (UT <= 16 && !a.exact)
+    if (!a.exact)
       err = launch_detect_warp(UT, el, x3, a, s);
     else
       err = launch_detect_tc(UT, el, x3, a, s, nullptr);
@@ -121,7 +127,7 @@ int precode_device(const cg_params* p, int64_t n_inst, const void* H, const void
     bool x3;
     tc_mode(p->precision, &el, &x3);
     const int UT = padded_users(p->U);
-    if (UT <= 16)
+    if (UT <= 32)
       err = launch_precode_warp(UT, el, x3, a, s);
     else
       err = launch_precode_tc(UT, el, x3, a, s, nullptr);

@@ -1,10 +1,12 @@
-// Warp-per-instance tensor-core kernels for CG-D and CG-P with up to 16 users.
+// Warp-per-instance tensor-core kernels for CG-D and CG-P with up to 32 users.
 //
 // One warp owns one instance (a channel H with its R <= 16 right-hand sides)
 // from its first load to its last store, so no CTA barrier is involved:
-//   1. H and Y (or T) are read straight from global memory into m16n8k16
-//      fragments with coalesced 16-byte loads, one k-step of 8 antennas
-//      ahead of the products that consume it;
+//   1. CG-D stages H and Y through a per-warp shared-memory ring of 16-byte
+//      cp.async copies, RING_STAGES k-steps of 8 antennas ahead of the
+//      products (the first stages of the next instance are issued before the
+//      CG of the current one); CG-P, which reads H a second time for
+//      q = H v, loads it with 16-byte register loads through L1;
 //   2. G = H^H H and the transposed matched filters B^T = Y^T conj(H)
 //      (Algorithm 1 line 5) accumulate on the tensor cores;
 //   3. Algorithm 1 lines 7-16 run entirely in registers. Users are numbered
@@ -16,9 +18,10 @@
 //   4. x_hat, mu, rho and the max-log LLRs of Eq. 4 (CG-D) or q = H v (CG-P,
 //      Algorithm 1 line 20) are stored from the registers that hold them.
 //
-// Position P (0 <= P < 8 NB) holds user pos_user(P); with 16 users the two
-// 8-blocks interleave (P = 8 nt + w holds user 2 w + nt), which makes the
-// users a lane touches contiguous in memory. Every product is a split
+// Position P (0 <= P < 8 NB) holds user pos_user(P). With 16 or 32 users the
+// 8-blocks interleave in pairs (P = 16 m + 8 h + w holds user 16 m + 2 w + h),
+// which makes the users a lane touches contiguous in memory; 32 users use
+// two 16-position m-tiles for the Gram rows. Every product is a split
 // (hi + lo) one in X3 mode, as in cg_tc.cuh; e = A p always is.
 #pragma once
 
@@ -35,15 +38,21 @@ constexpr int RING_STAGES = 4;
 
 template <int UT>
 struct WarpCfg {
-  static_assert(UT == 8 || UT == 16, "warp kernels serve 8 or 16 padded users");
-  static constexpr int NB = UT / 8;     // 8-position blocks
-  static constexpr int NFRAG = NB * NB * 2 * 2;  // CG B fragments: (ks, nt, b0/b1, re/im)
-  static constexpr int WARPS = 4;       // warps per CTA (independent)
+  static_assert(UT == 8 || UT == 16 || UT == 32, "warp kernels serve 8, 16 or 32 padded users");
+  static constexpr int NB = UT / 8;              // 8-position blocks
+  static constexpr int MT = UT == 32 ? 2 : 1;    // 16-position m-tiles of the Gram rows
+  static constexpr int PLANES = 2 * MT + 2;      // ring planes per stage: H rows, then Y
+  // The CG B fragments of A are kept hi|lo, and times i as well unless that
+  // would not fit (32 users form i A on the fly).
+  static constexpr bool STORE_IM = UT <= 16;
+  static constexpr int NFRAG = NB * NB * 2 * (STORE_IM ? 2 : 1);  // (ks, nt, b0/b1[, re/im])
+  static constexpr int WARPS = 4;                // warps per CTA (independent)
   static constexpr int NTHR = 32 * WARPS;
-  // per warp: a ring of RING_STAGES load stages (4 planes of 16 bytes per
-  // lane each), the CG B fragments (one uint2 per lane and fragment), and
+  static constexpr int MINB = UT == 32 ? 2 : CGM_WARP_MINB;  // resident CTAs per SM targeted
+  // per warp: a ring of RING_STAGES load stages (PLANES planes of 16 bytes
+  // per lane each), the CG B fragments (one uint2 per lane and fragment), and
   // alpha_k, beta_k of the 16 right-hand-side rows for the tracker (K <= UT)
-  static constexpr uint32_t RING_BYTES = uint32_t(RING_STAGES) * 4u * 32u * 16u;
+  static constexpr uint32_t RING_BYTES = uint32_t(RING_STAGES) * PLANES * 32u * 16u;
   static constexpr uint32_t FRAG_BYTES = uint32_t(NFRAG) * 32u * 8u;
   static constexpr uint32_t AB_BYTES = uint32_t(UT) * 16u * 8u;
   static constexpr uint32_t WARP_BYTES = RING_BYTES + FRAG_BYTES + AB_BYTES;
@@ -53,8 +62,15 @@ struct WarpCfg {
 
 template <int UT>
 __host__ __device__ constexpr int pos_user(int P) {
-  return UT == 16 ? 2 * (P & 7) + (P >> 3) : P;
+  return UT == 8 ? P : 16 * (P >> 4) + 2 * (P & 7) + ((P >> 3) & 1);
 }
+
+// Gram accumulators of a lane: [m-tile][n-tile][accumulator register].
+template <int UT>
+using GramAcc = float[WarpCfg<UT>::MT][UT / 8][4];
+// Matched-filter (or CG vector) accumulators: [n-tile][accumulator register].
+template <int UT>
+using VecAcc = float[UT / 8][4];
 
 __device__ __forceinline__ float4 ldg4(const float2* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -79,58 +95,68 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Stage `slot` of a warp ring: plane j of lane l at ring + (slot*4 + j)*512 + 16 l.
+// Stage `slot` of a warp ring: plane j of lane l at ring + (slot*PL + j)*512 + 16 l.
+template <int PL>
 __device__ __forceinline__ unsigned char* ring_at(unsigned char* ring, int slot, int plane) {
-  return ring + (slot * 4 + plane) * 512 + (threadIdx.x & 31) * 16;
+  return ring + (slot * PL + plane) * 512 + (threadIdx.x & 31) * 16;
 }
 
-// Issues one Gram k-step (antennas 8 ks + 2t, +1) into the ring: planes 0-1
-// the lane's H fragments, planes 2-3 (MF) its Y fragments; then commits a
-// group (an empty one when ks >= KS, which keeps the group count uniform).
-// Only the vector layout (U == UT, B even, 16-byte aligned) comes here.
+// Issues one Gram k-step (antennas 8 ks + 2t, +1) into the ring: planes
+// 2 m, 2 m + 1 the lane's H fragments of m-tile m, the last two (MF) its Y
+// fragments; then commits a group (an empty one when ks >= KS, which keeps
+// the group count uniform). Only the vector layout (U == UT, B even,
+// 16-byte aligned) comes here.
 template <int UT, bool MF>
 __device__ __forceinline__ void ring_gram_issue(unsigned char* ring, const float2* H,
                                                 const float2* Y, int B, int R, int KS, int ks) {
+  constexpr int PL = WarpCfg<UT>::PLANES, MT = WarpCfg<UT>::MT;
   if (ks < KS) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int slot = ks % RING_STAGES;
     const int b0 = 8 * ks + 2 * t, b1 = b0 + 1;
     const bool ok = b0 < B;
-    if constexpr (UT == 16) {
-      cp_async16(ring_at(ring, slot, 0), ok ? H + b0 * 16 + 2 * g : H, ok);
-      cp_async16(ring_at(ring, slot, 1), ok ? H + b1 * 16 + 2 * g : H, ok);
+    if constexpr (UT == 8) {
+      cp_async8(ring_at<PL>(ring, slot, 0), ok ? H + b0 * 8 + g : H, ok);
+      cp_async8(ring_at<PL>(ring, slot, 1), ok ? H + b1 * 8 + g : H, ok);
     } else {
-      cp_async8(ring_at(ring, slot, 0), ok ? H + b0 * 8 + g : H, ok);
-      cp_async8(ring_at(ring, slot, 1), ok ? H + b1 * 8 + g : H, ok);
+#pragma unroll
+      for (int m = 0; m < MT; ++m) {
+        cp_async16(ring_at<PL>(ring, slot, 2 * m), ok ? H + b0 * UT + 16 * m + 2 * g : H, ok);
+        cp_async16(ring_at<PL>(ring, slot, 2 * m + 1), ok ? H + b1 * UT + 16 * m + 2 * g : H, ok);
+      }
     }
     if constexpr (MF) {
       const bool ok0 = ok && g < R, ok1 = ok && g + 8 < R;
-      cp_async16(ring_at(ring, slot, 2), ok0 ? Y + g * B + b0 : Y, ok0);
-      cp_async16(ring_at(ring, slot, 3), ok1 ? Y + (g + 8) * B + b0 : Y, ok1);
+      cp_async16(ring_at<PL>(ring, slot, 2 * MT), ok0 ? Y + g * B + b0 : Y, ok0);
+      cp_async16(ring_at<PL>(ring, slot, 2 * MT + 1), ok1 ? Y + (g + 8) * B + b0 : Y, ok1);
     }
   }
   cp_commit();
 }
 
 template <int UT, bool MF>
-__device__ __forceinline__ void ring_gram_read(unsigned char* ring, int ks, float2 (&h)[4],
-                                               float2 (&y)[4]) {
+__device__ __forceinline__ void ring_gram_read(unsigned char* ring, int ks,
+                                               float2 (&h)[WarpCfg<UT>::MT][4], float2 (&y)[4]) {
+  constexpr int PL = WarpCfg<UT>::PLANES, MT = WarpCfg<UT>::MT;
   const int slot = ks % RING_STAGES;
-  if constexpr (UT == 16) {
-    const float4 v0 = *reinterpret_cast<const float4*>(ring_at(ring, slot, 0));
-    const float4 v1 = *reinterpret_cast<const float4*>(ring_at(ring, slot, 1));
-    h[0] = make_float2(v0.x, v0.y);
-    h[1] = make_float2(v0.z, v0.w);
-    h[2] = make_float2(v1.x, v1.y);
-    h[3] = make_float2(v1.z, v1.w);
+  if constexpr (UT == 8) {
+    h[0][0] = *reinterpret_cast<const float2*>(ring_at<PL>(ring, slot, 0));
+    h[0][2] = *reinterpret_cast<const float2*>(ring_at<PL>(ring, slot, 1));
+    h[0][1] = h[0][3] = make_float2(0.f, 0.f);
   } else {
-    h[0] = *reinterpret_cast<const float2*>(ring_at(ring, slot, 0));
-    h[2] = *reinterpret_cast<const float2*>(ring_at(ring, slot, 1));
-    h[1] = h[3] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const float4 v0 = *reinterpret_cast<const float4*>(ring_at<PL>(ring, slot, 2 * m));
+      const float4 v1 = *reinterpret_cast<const float4*>(ring_at<PL>(ring, slot, 2 * m + 1));
+      h[m][0] = make_float2(v0.x, v0.y);
+      h[m][1] = make_float2(v0.z, v0.w);
+      h[m][2] = make_float2(v1.x, v1.y);
+      h[m][3] = make_float2(v1.z, v1.w);
+    }
   }
   if constexpr (MF) {
-    const float4 w0 = *reinterpret_cast<const float4*>(ring_at(ring, slot, 2));
-    const float4 w1 = *reinterpret_cast<const float4*>(ring_at(ring, slot, 3));
+    const float4 w0 = *reinterpret_cast<const float4*>(ring_at<PL>(ring, slot, 2 * MT));
+    const float4 w1 = *reinterpret_cast<const float4*>(ring_at<PL>(ring, slot, 2 * MT + 1));
     y[0] = make_float2(w0.x, w0.y);
     y[2] = make_float2(w0.z, w0.w);
     y[1] = make_float2(w1.x, w1.y);
@@ -148,17 +174,22 @@ __device__ __forceinline__ void ring_gram_prologue(unsigned char* ring, const fl
 }
 
 // q = H v n-tile nb (antennas 8 nb + g): the lane's H entries of users
-// 4t..4t+3 (16 users: two 16-byte loads) or 2t..2t+1 (8 users: one).
+// 16 m + 4t..4t+3 for each m-tile m (two 16-byte loads each; 8 users: one
+// load of users 2t, 2t+1).
 template <int UT>
-__device__ __forceinline__ void q_load(const float2* H, int B, int nb, int g, int t, float4& f0,
-                                       float4& f1) {
+__device__ __forceinline__ void q_load(const float2* H, int B, int nb, int g, int t,
+                                       float4 (&f)[WarpCfg<UT>::MT][2]) {
+  constexpr int MT = WarpCfg<UT>::MT;
   const int b = 8 * nb + g;
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (b < B) {
-    f0 = ldg4(H + b * UT + (UT == 16 ? 4 : 2) * t);
-    f1 = UT == 16 ? ldg4(H + b * UT + 4 * t + 2) : zero4;
-  } else {
-    f0 = f1 = zero4;
+#pragma unroll
+  for (int m = 0; m < MT; ++m) {
+    if (b < B) {
+      f[m][0] = ldg4(H + b * UT + 16 * m + (UT == 8 ? 2 : 4) * t);
+      f[m][1] = UT == 8 ? zero4 : ldg4(H + b * UT + 16 * m + 4 * t + 2);
+    } else {
+      f[m][0] = f[m][1] = zero4;
+    }
   }
 }
 
@@ -189,38 +220,46 @@ __device__ __forceinline__ void quad_sum2(float& x0, float& x1) {
 // Loads of one k-step (antennas b0 = 8 ks + 2 t and b0 + 1)
 // ---------------------------------------------------------------------------
 
-// h[0..3]: H(b0, row user 0), H(b0, row user 1), H(b0+1, row user 0),
-// H(b0+1, row user 1); the row users of lane g are 2g, 2g+1 (16) or g (8).
+// h[m][0..3]: H(b0, row user 0), H(b0, row user 1), H(b0+1, row user 0),
+// H(b0+1, row user 1) of m-tile m; the row users of lane g are 16 m + 2g,
+// 16 m + 2g + 1 (16 and 32 users) or g (8 users; row user 1 absent).
 // VEC: U == UT, B even, H 16-byte aligned.
 template <int UT, bool VEC>
 __device__ __forceinline__ void load_h_ks(const float2* __restrict__ H, int B, int U, int ks,
-                                          int g, int t, float2 (&h)[4]) {
+                                          int g, int t, float2 (&h)[WarpCfg<UT>::MT][4]) {
+  constexpr int MT = WarpCfg<UT>::MT;
   const int b0 = 8 * ks + 2 * t, b1 = b0 + 1;
   const float2 z = make_float2(0.f, 0.f);
   if constexpr (VEC) {
     const bool ok = b0 < B;
-    if constexpr (UT == 16) {
-      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 v0 = ok ? ldg4(H + b0 * 16 + 2 * g) : zero4;
-      const float4 v1 = ok ? ldg4(H + b1 * 16 + 2 * g) : zero4;
-      h[0] = make_float2(v0.x, v0.y);
-      h[1] = make_float2(v0.z, v0.w);
-      h[2] = make_float2(v1.x, v1.y);
-      h[3] = make_float2(v1.z, v1.w);
+    if constexpr (UT == 8) {
+      h[0][0] = ok ? ldg2(H + b0 * 8 + g) : z;
+      h[0][2] = ok ? ldg2(H + b1 * 8 + g) : z;
+      h[0][1] = h[0][3] = z;
     } else {
-      h[0] = ok ? ldg2(H + b0 * 8 + g) : z;
-      h[2] = ok ? ldg2(H + b1 * 8 + g) : z;
-      h[1] = h[3] = z;
+      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int m = 0; m < MT; ++m) {
+        const float4 v0 = ok ? ldg4(H + b0 * UT + 16 * m + 2 * g) : zero4;
+        const float4 v1 = ok ? ldg4(H + b1 * UT + 16 * m + 2 * g) : zero4;
+        h[m][0] = make_float2(v0.x, v0.y);
+        h[m][1] = make_float2(v0.z, v0.w);
+        h[m][2] = make_float2(v1.x, v1.y);
+        h[m][3] = make_float2(v1.z, v1.w);
+      }
     }
   } else {
-    const int u0 = UT == 16 ? 2 * g : g, u1 = 2 * g + 1;
-    h[0] = (b0 < B && u0 < U) ? ldg2(H + b0 * U + u0) : z;
-    h[2] = (b1 < B && u0 < U) ? ldg2(H + b1 * U + u0) : z;
-    if constexpr (UT == 16) {
-      h[1] = (b0 < B && u1 < U) ? ldg2(H + b0 * U + u1) : z;
-      h[3] = (b1 < B && u1 < U) ? ldg2(H + b1 * U + u1) : z;
-    } else {
-      h[1] = h[3] = z;
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const int u0 = UT == 8 ? g : 16 * m + 2 * g, u1 = 16 * m + 2 * g + 1;
+      h[m][0] = (b0 < B && u0 < U) ? ldg2(H + b0 * U + u0) : z;
+      h[m][2] = (b1 < B && u0 < U) ? ldg2(H + b1 * U + u0) : z;
+      if constexpr (UT != 8) {
+        h[m][1] = (b0 < B && u1 < U) ? ldg2(H + b0 * U + u1) : z;
+        h[m][3] = (b1 < B && u1 < U) ? ldg2(H + b1 * U + u1) : z;
+      } else {
+        h[m][1] = h[m][3] = z;
+      }
     }
   }
 }
@@ -253,19 +292,19 @@ __device__ __forceinline__ void load_y_ks(const float2* __restrict__ Y, int B, i
 // Gram (and transposed matched filters) of one k-step
 // ---------------------------------------------------------------------------
 
-// Gr/Gi[nt][d]: G at row position 8 (d >> 1) + g, column position
+// Gr/Gi[m][nt][d]: G at row position 16 m + 8 (d >> 1) + g, column position
 // 8 nt + 2 t + (d & 1). Mr[nt][d] = Re b^T and Mn[nt][d] = -Im b^T at
 // right-hand side g + 8 (d >> 1), column position 8 nt + 2 t + (d & 1).
 template <int UT, int EL, bool X3, bool MF>
-__device__ __forceinline__ void gram_ks(const float2 (&h)[4], const float2 (&y)[4],
-                                        float (&Gr)[UT / 8][4], float (&Gi)[UT / 8][4],
-                                        float (&Mr)[UT / 8][4], float (&Mn)[UT / 8][4]) {
-  constexpr int NB = UT / 8;
-  uint2 hs[4];
+__device__ __forceinline__ void gram_ks(const float2 (&h)[WarpCfg<UT>::MT][4],
+                                        const float2 (&y)[4], GramAcc<UT>& Gr, GramAcc<UT>& Gi,
+                                        VecAcc<UT>& Mr, VecAcc<UT>& Mn) {
+  constexpr int NB = UT / 8, MT = WarpCfg<UT>::MT;
+  uint2 hs[MT][4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) hs[k] = split_c<EL>(h[k]);
-  const uint32_t ah[4] = {hs[0].x, hs[1].x, hs[2].x, hs[3].x};
-  const uint32_t al[4] = {hs[0].y, hs[1].y, hs[2].y, hs[3].y};
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) hs[m][k] = split_c<EL>(h[m][k]);
   uint32_t yh[4], yl[4];
   if constexpr (MF) {
 #pragma unroll
@@ -278,11 +317,17 @@ __device__ __forceinline__ void gram_ks(const float2 (&h)[4], const float2 (&y)[
 #pragma unroll
   for (int nt = 0; nt < NB; ++nt) {
     // B fragments of n-tile nt: the row-user registers of block nt
-    const uint2 b0 = hs[nt], b1 = hs[2 + nt];
+    // (m-tile nt / 2, row half nt % 2)
+    const uint2 b0 = hs[nt >> 1][nt & 1], b1 = hs[nt >> 1][2 + (nt & 1)];
     const uint32_t s0h = swap_neg(b0.x), s1h = swap_neg(b1.x);
     const uint32_t s0l = swap_neg(b0.y), s1l = swap_neg(b1.y);
-    mma_split<EL, X3>(Gr[nt], ah, al, b0.x, b1.x, b0.y, b1.y);
-    mma_split<EL, X3>(Gi[nt], ah, al, s0h, s1h, s0l, s1l);
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const uint32_t ah[4] = {hs[m][0].x, hs[m][1].x, hs[m][2].x, hs[m][3].x};
+      const uint32_t al[4] = {hs[m][0].y, hs[m][1].y, hs[m][2].y, hs[m][3].y};
+      mma_split<EL, X3>(Gr[m][nt], ah, al, b0.x, b1.x, b0.y, b1.y);
+      mma_split<EL, X3>(Gi[m][nt], ah, al, s0h, s1h, s0l, s1l);
+    }
     if constexpr (MF) {
       mma_split<EL, X3>(Mr[nt], yh, yl, b0.x, b1.x, b0.y, b1.y);
       mma_split<EL, X3>(Mn[nt], yh, yl, s0h, s1h, s0l, s1l);
@@ -295,11 +340,13 @@ __device__ __forceinline__ void gram_ks(const float2 (&h)[4], const float2 (&y)[
 // ---------------------------------------------------------------------------
 
 // CG state of one warp: entry [h][nt][c] is right-hand side g + 8 h at
-// position 8 nt + 2 t + c. The B fragments of A (plain and times i, hi|lo)
-// live in this warp's shared-memory slice, one uint2 per lane and fragment.
+// position 8 nt + 2 t + c. The B fragments of A (hi|lo, and times i when
+// WarpCfg::STORE_IM) live in this warp's shared-memory slice, one uint2 per
+// lane and fragment.
 template <int UT, int EL>
 struct WarpCg {
   static constexpr int NB = UT / 8;
+  static constexpr bool STORE_IM = WarpCfg<UT>::STORE_IM;
   float2 v[2][NB][2], res[2][NB][2], p[2][NB][2];
   float D[NB][2];
   float rrn[2];
@@ -308,12 +355,13 @@ struct WarpCg {
 
   // Fragment index of (ks, nt, b, part) in the shared slice.
   __device__ __forceinline__ static int fidx(int ks, int nt, int b, int part) {
-    return ((ks * NB + nt) * 2 + b) * 2 + part;
+    return STORE_IM ? ((ks * NB + nt) * 2 + b) * 2 + part : (ks * NB + nt) * 2 + b;
   }
 
   // Writes A = G + sigma I as B fragments (from the Gram accumulators) and
-  // returns D = diag(A) and G_ii at the lane's positions.
-  __device__ __forceinline__ static void setup_a(const float (&Gr)[NB][4], const float (&Gi)[NB][4],
+  // returns D = diag(A) and G_ii at the lane's positions. Row 8 nt + g of
+  // the Gram is row half nt % 2 of m-tile nt / 2.
+  __device__ __forceinline__ static void setup_a(const GramAcc<UT>& Gr, const GramAcc<UT>& Gi,
                                                  float sigma, uint2* frag, float (&Dout)[NB][2],
                                                  float (&Gd)[NB][2]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -324,18 +372,20 @@ struct WarpCg {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           // A[8 ks + 2 t + b][8 nt + g] = conj(G[8 nt + g][8 ks + 2 t + b]) (+ sigma)
-          const int d = 2 * nt + b;
+          const int m = nt >> 1, d = 2 * (nt & 1) + b;
           const bool diag = (ks == nt) && (g == 2 * t + b);
-          const float re = Gr[ks][d] + (diag ? sigma : 0.f);
-          const float im = diag ? 0.f : -Gi[ks][d];
+          const float re = Gr[m][ks][d] + (diag ? sigma : 0.f);
+          const float im = diag ? 0.f : -Gi[m][ks][d];
           frag[fidx(ks, nt, b, 0) * 32 + lane] = split_c<EL>(make_float2(re, im));
-          frag[fidx(ks, nt, b, 1) * 32 + lane] = split_c<EL>(make_float2(-im, re));
+          if constexpr (STORE_IM)
+            frag[fidx(ks, nt, b, 1) * 32 + lane] = split_c<EL>(make_float2(-im, re));
         }
 #pragma unroll
     for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const float gd = __shfl_sync(0xffffffffu, Gr[nt][2 * nt + c], 4 * (2 * t + c) + t);
+        const float gd = __shfl_sync(0xffffffffu, Gr[nt >> 1][nt][2 * (nt & 1) + c],
+                                     4 * (2 * t + c) + t);
         Gd[nt][c] = gd;
         Dout[nt][c] = gd + sigma;
       }
@@ -365,8 +415,14 @@ struct WarpCg {
       for (int ks = 0; ks < NB; ++ks) {
         const uint2 r0 = frag[fidx(ks, nt, 0, 0) * 32 + lane];
         const uint2 r1 = frag[fidx(ks, nt, 1, 0) * 32 + lane];
-        const uint2 i0 = frag[fidx(ks, nt, 0, 1) * 32 + lane];
-        const uint2 i1 = frag[fidx(ks, nt, 1, 1) * 32 + lane];
+        uint2 i0, i1;
+        if constexpr (STORE_IM) {
+          i0 = frag[fidx(ks, nt, 0, 1) * 32 + lane];
+          i1 = frag[fidx(ks, nt, 1, 1) * 32 + lane];
+        } else {  // i (re, im) = (-im, re): swap the halves, negate the new low one
+          i0 = make_uint2(swap_halves(r0.x) ^ 0x8000u, swap_halves(r0.y) ^ 0x8000u);
+          i1 = make_uint2(swap_halves(r1.x) ^ 0x8000u, swap_halves(r1.y) ^ 0x8000u);
+        }
         mma16816<EL>(rh, ph[ks], r0.x, r1.x);
         mma16816<EL>(ih, ph[ks], i0.x, i1.x);
         mma16816<EL>(rx, ph[ks], r0.y, r1.y);
@@ -596,63 +652,68 @@ __device__ __forceinline__ void store_row_detect(const DetItem& it, int r, int t
                                                  const float (&mu)[UT / 8][2],
                                                  const float (&rho)[UT / 8][2], float cq,
                                                  int* flags) {
-  constexpr int NB = UT / 8, NU = 2 * NB, H = QB / 2;
-  const int u0 = UT == 16 ? 4 * t : 2 * t;
-  const int64_t base = int64_t(r) * it.U + u0;
-  float2 xo[NU];
-  float mo[NU], ro[NU];
+  constexpr int MT = WarpCfg<UT>::MT, NUG = UT == 8 ? 2 : 4, H = QB / 2;
 #pragma unroll
-  for (int m = 0; m < NU; ++m) {
-    const int nt = UT == 16 ? (m & 1) : 0, c = UT == 16 ? (m >> 1) : m;
-    xo[m] = x[nt][c];
-    mo[m] = mu[nt][c];
-    ro[m] = rho[nt][c];
-  }
-  if constexpr (VEC) {
-    if (it.xhat) {
-      float4* xp = reinterpret_cast<float4*>(it.xhat + base);
+  for (int gr = 0; gr < MT; ++gr) {
+    // users 16 gr + 4t + m (m = 2c + nt % 2, nt = 2 gr + m % 2), or 2t + m
+    const int u0 = UT == 8 ? 2 * t : 16 * gr + 4 * t;
+    const int64_t base = int64_t(r) * it.U + u0;
+    float2 xo[NUG];
+    float mo[NUG], ro[NUG];
 #pragma unroll
-      for (int m = 0; m < NU; m += 2)
-        xp[m / 2] = make_float4(xo[m].x, xo[m].y, xo[m + 1].x, xo[m + 1].y);
+    for (int m = 0; m < NUG; ++m) {
+      const int nt = UT == 8 ? 0 : 2 * gr + (m & 1), c = UT == 8 ? m : (m >> 1);
+      xo[m] = x[nt][c];
+      mo[m] = mu[nt][c];
+      ro[m] = rho[nt][c];
     }
-    if constexpr (NU == 4) {
-      if (it.mu) *reinterpret_cast<float4*>(it.mu + base) = make_float4(mo[0], mo[1], mo[2], mo[3]);
-      if (it.rho)
-        *reinterpret_cast<float4*>(it.rho + base) = make_float4(ro[0], ro[1], ro[2], ro[3]);
-    } else {
-      if (it.mu) *reinterpret_cast<float2*>(it.mu + base) = make_float2(mo[0], mo[1]);
-      if (it.rho) *reinterpret_cast<float2*>(it.rho + base) = make_float2(ro[0], ro[1]);
-    }
-  }
+    if constexpr (VEC) {
+      if (it.xhat) {
+        float4* xp = reinterpret_cast<float4*>(it.xhat + base);
 #pragma unroll
-  for (int m = 0; m < NU; ++m) {
-    const bool in = VEC || u0 + m < it.U;
-    if (!in) continue;
-    const bool valid = mo[m] > 0.f;
-    if (!valid) *flags |= ST_MU_NONPOS;
-    const int64_t o = base + m;
-    if constexpr (!VEC) {
-      if (it.xhat) it.xhat[o] = xo[m];
-      if (it.mu) it.mu[o] = mo[m];
-      if (it.rho) it.rho[o] = ro[m];
-    }
-    if (it.llr) {
-      float lI[H], lQ[H];
-      if (valid) {
-        const float inv = __frcp_rn(mo[m] * cq);  // u = x_hat / (mu c)
-        const float scale = ro[m] * cq * cq;
-        axis_llr_gray<H>(xo[m].x * inv, scale, lI);
-        axis_llr_gray<H>(xo[m].y * inv, scale, lQ);
-      } else {
-#pragma unroll
-        for (int k = 0; k < H; ++k) lI[k] = lQ[k] = 0.f;
+        for (int m = 0; m < NUG; m += 2)
+          xp[m / 2] = make_float4(xo[m].x, xo[m].y, xo[m + 1].x, xo[m + 1].y);
       }
-      float2* lp = reinterpret_cast<float2*>(it.llr + o * QB);
+      if constexpr (NUG == 4) {
+        if (it.mu)
+          *reinterpret_cast<float4*>(it.mu + base) = make_float4(mo[0], mo[1], mo[2], mo[3]);
+        if (it.rho)
+          *reinterpret_cast<float4*>(it.rho + base) = make_float4(ro[0], ro[1], ro[2], ro[3]);
+      } else {
+        if (it.mu) *reinterpret_cast<float2*>(it.mu + base) = make_float2(mo[0], mo[1]);
+        if (it.rho) *reinterpret_cast<float2*>(it.rho + base) = make_float2(ro[0], ro[1]);
+      }
+    }
 #pragma unroll
-      for (int k = 0; k < H; ++k) {
-        const float a = 2 * k < H ? lI[2 * k] : lQ[2 * k - H];
-        const float b = 2 * k + 1 < H ? lI[2 * k + 1] : lQ[2 * k + 1 - H];
-        lp[k] = make_float2(a, b);
+    for (int m = 0; m < NUG; ++m) {
+      const bool in = VEC || u0 + m < it.U;
+      if (!in) continue;
+      const bool valid = mo[m] > 0.f;
+      if (!valid) *flags |= ST_MU_NONPOS;
+      const int64_t o = base + m;
+      if constexpr (!VEC) {
+        if (it.xhat) it.xhat[o] = xo[m];
+        if (it.mu) it.mu[o] = mo[m];
+        if (it.rho) it.rho[o] = ro[m];
+      }
+      if (it.llr) {
+        float lI[H], lQ[H];
+        if (valid) {
+          const float inv = __frcp_rn(mo[m] * cq);  // u = x_hat / (mu c)
+          const float scale = ro[m] * cq * cq;
+          axis_llr_gray<H>(xo[m].x * inv, scale, lI);
+          axis_llr_gray<H>(xo[m].y * inv, scale, lQ);
+        } else {
+#pragma unroll
+          for (int k = 0; k < H; ++k) lI[k] = lQ[k] = 0.f;
+        }
+        float2* lp = reinterpret_cast<float2*>(it.llr + o * QB);
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          const float a = 2 * k < H ? lI[2 * k] : lQ[2 * k - H];
+          const float b = 2 * k + 1 < H ? lI[2 * k + 1] : lQ[2 * k + 1 - H];
+          lp[k] = make_float2(a, b);
+        }
       }
     }
   }
@@ -670,27 +731,30 @@ enum : int { LD_RING = 0, LD_VEC = 1, LD_ELEM = 2 };
 // Algorithm 1 line 5: G and b^T on the tensor cores.
 template <int UT, int EL, bool X3, int LD, bool MF>
 __device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int B, int U, int R,
-                                          unsigned char* ring, float (&Gr)[UT / 8][4],
-                                          float (&Gi)[UT / 8][4], float (&Mr)[UT / 8][4],
-                                          float (&Mn)[UT / 8][4]) {
-  constexpr int NB = UT / 8;
+                                          unsigned char* ring, GramAcc<UT>& Gr, GramAcc<UT>& Gi,
+                                          VecAcc<UT>& Mr, VecAcc<UT>& Mn) {
+  constexpr int NB = UT / 8, MT = WarpCfg<UT>::MT;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
   for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) Gr[nt][k] = Gi[nt][k] = Mr[nt][k] = Mn[nt][k] = 0.f;
+    for (int k = 0; k < 4; ++k) {
+      Mr[nt][k] = Mn[nt][k] = 0.f;
+#pragma unroll
+      for (int m = 0; m < MT; ++m) Gr[m][nt][k] = Gi[m][nt][k] = 0.f;
+    }
   const int KS = (B + 7) / 8;
   if constexpr (LD == LD_RING) {
     for (int ks = 0; ks < KS; ++ks) {
       ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, ks + RING_STAGES - 1);
       cp_wait<RING_STAGES - 1>();
-      float2 h[4], y[4];
+      float2 h[MT][4], y[4];
       ring_gram_read<UT, MF>(ring, ks, h, y);
       gram_ks<UT, EL, X3, MF>(h, y, Gr, Gi, Mr, Mn);
     }
   } else {
     constexpr bool V = LD == LD_VEC;
-    float2 ha[4], ya[4] = {}, hb[4], yb[4] = {};
+    float2 ha[MT][4], ya[4] = {}, hb[MT][4], yb[4] = {};
     load_h_ks<UT, V>(H, B, U, 0, g, t, ha);
     if constexpr (MF) load_y_ks<V>(Y, B, R, 0, g, t, ya);
     for (int ks = 0; ks < KS; ks += 2) {  // ping-pong: loads run one k-step ahead
@@ -712,10 +776,8 @@ __device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int 
 // Lines 7-19 and Eq. 4 of one instance whose Gram and matched filters are done.
 template <int UT, int EL, bool VEC>
 __device__ __forceinline__ int detect_warp_finish(const DetItem& it, uint2* frag, float2* sAB,
-                                                  const float (&Gr)[UT / 8][4],
-                                                  const float (&Gi)[UT / 8][4],
-                                                  const float (&Mr)[UT / 8][4],
-                                                  const float (&Mn)[UT / 8][4]) {
+                                                  const GramAcc<UT>& Gr, const GramAcc<UT>& Gi,
+                                                  const VecAcc<UT>& Mr, const VecAcc<UT>& Mn) {
   constexpr int NB = UT / 8;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   WarpCg<UT, EL> cg;
@@ -791,11 +853,9 @@ __device__ __forceinline__ int64_t warp_next_early(const S& s, int64_t cur, int6
 // Instance loop: the Gram of an instance, then the next instance's first
 // load stages, then the CG and outputs (which overlap those loads).
 template <int UT, int EL, bool X3, class Src>
-__device__ __forceinline__ void detect_warp_body(const Src& src) {
+__device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* mine) {
   constexpr int NB = UT / 8;
-  extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
-  unsigned char* mine = smem + warp * WarpCfg<UT>::WARP_BYTES;
   unsigned char* ring = mine;
   uint2* frag = reinterpret_cast<uint2*>(mine + WarpCfg<UT>::RING_BYTES);
   float2* sAB = reinterpret_cast<float2*>(mine + WarpCfg<UT>::RING_BYTES + WarpCfg<UT>::FRAG_BYTES);
@@ -808,7 +868,8 @@ __device__ __forceinline__ void detect_warp_body(const Src& src) {
     if (vec) ring_gram_prologue<UT, true>(ring, it.H, it.Y, it.B, it.R);
   }
   while (cur >= 0) {
-    float Gr[NB][4], Gi[NB][4], Mr[NB][4], Mn[NB][4];
+    GramAcc<UT> Gr, Gi;
+    VecAcc<UT> Mr, Mn;
     {
       const DetItem it = det_item(src, cur);
       if (vec)
@@ -855,8 +916,7 @@ __device__ __forceinline__ void detect_warp_body(const Src& src) {
 // Gram is done.
 template <int UT, int EL, bool X3, bool VEC>
 __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* frag,
-                                                   const float (&Gr)[UT / 8][4],
-                                                   const float (&Gi)[UT / 8][4]) {
+                                                   const GramAcc<UT>& Gr, const GramAcc<UT>& Gi) {
   constexpr int NB = UT / 8;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   WarpCg<UT, EL> cg;
@@ -927,26 +987,34 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
   }
   // H is read a second time here (L1 or L2: the Gram read it moments ago);
   // VEC keeps the 16-byte loads of the next n-tile in flight.
+  constexpr int MT = WarpCfg<UT>::MT;
   const int NBQ = (it.B + 7) / 8;
-  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 fa0 = zero4, fa1 = zero4;
-  if constexpr (VEC) q_load<UT>(it.H, it.B, 0, g, t, fa0, fa1);
+  float4 fa[MT][2];
+  if constexpr (VEC) q_load<UT>(it.H, it.B, 0, g, t, fa);
   for (int nb = 0; nb < NBQ; ++nb) {
     const int b = 8 * nb + g;
     // lane's H entries at its k-positions: e[ks][j] = H(b, user(8 ks + 2 t + j))
     float2 e[NB][2];
     const float2 z = make_float2(0.f, 0.f);
     if constexpr (VEC) {
-      const float4 f0 = fa0, f1 = fa1;
-      if (nb + 1 < NBQ) q_load<UT>(it.H, it.B, nb + 1, g, t, fa0, fa1);
-      if constexpr (UT == 16) {
-        e[0][0] = make_float2(f0.x, f0.y);  // user 4t
-        e[1][0] = make_float2(f0.z, f0.w);  // user 4t + 1
-        e[0][1] = make_float2(f1.x, f1.y);  // user 4t + 2
-        e[1][1] = make_float2(f1.z, f1.w);  // user 4t + 3
+      float4 f[MT][2];
+#pragma unroll
+      for (int m = 0; m < MT; ++m) {
+        f[m][0] = fa[m][0];
+        f[m][1] = fa[m][1];
+      }
+      if (nb + 1 < NBQ) q_load<UT>(it.H, it.B, nb + 1, g, t, fa);
+      if constexpr (UT == 8) {
+        e[0][0] = make_float2(f[0][0].x, f[0][0].y);
+        e[0][1] = make_float2(f[0][0].z, f[0][0].w);
       } else {
-        e[0][0] = make_float2(f0.x, f0.y);
-        e[0][1] = make_float2(f0.z, f0.w);
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+          e[2 * m][0] = make_float2(f[m][0].x, f[m][0].y);      // user 16m + 4t
+          e[2 * m + 1][0] = make_float2(f[m][0].z, f[m][0].w);  // user 16m + 4t + 1
+          e[2 * m][1] = make_float2(f[m][1].x, f[m][1].y);      // user 16m + 4t + 2
+          e[2 * m + 1][1] = make_float2(f[m][1].z, f[m][1].w);  // user 16m + 4t + 3
+        }
       }
     } else {
 #pragma unroll
@@ -998,16 +1066,16 @@ __device__ __forceinline__ bool precode_vec(const PreItem& it) {
 // Instance loop. CG-P reads H twice (Gram, then q = H v); both passes use
 // 16-byte register loads through L1, where the second pass finds part of H.
 template <int UT, int EL, bool X3, class Src>
-__device__ __forceinline__ void precode_warp_body(const Src& src) {
+__device__ __forceinline__ void precode_warp_body(const Src& src, unsigned char* mine) {
   constexpr int NB = UT / 8;
-  extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
-  uint2* frag = reinterpret_cast<uint2*>(smem + warp * WarpCfg<UT>::FRAG_BYTES);
+  uint2* frag = reinterpret_cast<uint2*>(mine);
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
   int64_t cur = warp_first(src, int64_t(blockIdx.x) * (blockDim.x >> 5) + warp);
   while (cur >= 0) {
     const PreItem it = pre_item(src, cur);
-    float Gr[NB][4], Gi[NB][4], Mr[NB][4], Mn[NB][4];
+    GramAcc<UT> Gr, Gi;
+    VecAcc<UT> Mr, Mn;
     int st;
     if (precode_vec<UT>(it)) {
       warp_gram<UT, EL, X3, LD_VEC, false>(it.H, nullptr, it.B, it.U, 0, nullptr, Gr, Gi, Mr, Mn);
@@ -1028,35 +1096,139 @@ __device__ __forceinline__ void precode_warp_body(const Src& src) {
   }
 }
 
+// This warp's slice of the dynamic shared memory.
+template <uint32_t SLICE>
+__device__ __forceinline__ unsigned char* warp_slice() {
+  extern __shared__ __align__(128) unsigned char smem[];
+  return smem + (threadIdx.x >> 5) * SLICE;
+}
+
 template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB) detect_warp_kernel(const DetectArgs a) {
-  detect_warp_body<UT, EL, X3>(a);
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, WarpCfg<UT>::MINB) detect_warp_kernel(const DetectArgs a) {
+  detect_warp_body<UT, EL, X3>(a, warp_slice<WarpCfg<UT>::WARP_BYTES>());
 }
 template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB) precode_warp_kernel(const PrecodeArgs a) {
-  precode_warp_body<UT, EL, X3>(a);
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, WarpCfg<UT>::MINB) precode_warp_kernel(const PrecodeArgs a) {
+  precode_warp_body<UT, EL, X3>(a, warp_slice<WarpCfg<UT>::FRAG_BYTES>());
 }
 template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB) detect_warp_batch_kernel(const BatchArgs b) {
-  detect_warp_body<UT, EL, X3>(b);
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, WarpCfg<UT>::MINB) detect_warp_batch_kernel(const BatchArgs b) {
+  detect_warp_body<UT, EL, X3>(b, warp_slice<WarpCfg<UT>::WARP_BYTES>());
 }
 template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB)
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, WarpCfg<UT>::MINB)
     precode_warp_batch_kernel(const BatchArgs b) {
-  precode_warp_body<UT, EL, X3>(b);
+  precode_warp_body<UT, EL, X3>(b, warp_slice<WarpCfg<UT>::FRAG_BYTES>());
+}
+
+// ---------------------------------------------------------------------------
+// Serving: one kernel for the six (operation, padded users) classes of the
+// approximate tracker
+// ---------------------------------------------------------------------------
+
+// Classes 0-2 detect with 8, 16, 32 padded users, 3-5 precode.
+constexpr int kWarpClasses = 6;
+// Every warp owns a slice large enough for any class, since the warps of one
+// CTA may serve different classes at the same time.
+constexpr uint32_t kServeSlice = WarpCfg<32>::WARP_BYTES;
+static_assert(WarpCfg<8>::WARP_BYTES <= kServeSlice && WarpCfg<16>::WARP_BYTES <= kServeSlice &&
+                  WarpCfg<32>::FRAG_BYTES <= kServeSlice,
+              "serving slice must hold every class");
+
+// Kernel parameters: the kernel's own ServeArgs (cls = its liveness counter,
+// idle_ns = its idle limit) and one copy per class with cls = the class and
+// idle_ns = 0, so that a class body returns once its class has no work. The
+// copies live in the parameter space, which the bodies read in place.
+struct ServeWarpArgs {
+  ServeArgs k;
+  ServeArgs c[kWarpClasses];
+};
+
+// One class body as a called function, so that each class keeps the
+// register allocation it has in its own kernel.
+template <int UT, int EL, bool X3>
+__device__ __noinline__ void serve_detect(const ServeArgs& s, unsigned char* mine) {
+  detect_warp_body<UT, EL, X3>(s, mine);
 }
 template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB) detect_warp_serve_kernel(const ServeArgs s) {
-  if ((threadIdx.x & 31) == 0) serve_unit_enter(s);
-  detect_warp_body<UT, EL, X3>(s);
-  if ((threadIdx.x & 31) == 0) serve_unit_exit(s);
+__device__ __noinline__ void serve_precode(const ServeArgs& s, unsigned char* mine) {
+  precode_warp_body<UT, EL, X3>(s, mine);
 }
-template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, CGM_WARP_MINB)
-    precode_warp_serve_kernel(const ServeArgs s) {
-  if ((threadIdx.x & 31) == 0) serve_unit_enter(s);
-  precode_warp_body<UT, EL, X3>(s);
-  if ((threadIdx.x & 31) == 0) serve_unit_exit(s);
+
+template <int EL, bool X3>
+__device__ __forceinline__ void serve_class(int c, const ServeWarpArgs& p, unsigned char* mine) {
+  switch (c) {
+    case 0: serve_detect<8, EL, X3>(p.c[0], mine); break;
+    case 1: serve_detect<16, EL, X3>(p.c[1], mine); break;
+    case 2: serve_detect<32, EL, X3>(p.c[2], mine); break;
+    case 3: serve_precode<8, EL, X3>(p.c[3], mine); break;
+    case 4: serve_precode<16, EL, X3>(p.c[4], mine); break;
+    default: serve_precode<32, EL, X3>(p.c[5], mine); break;
+  }
+}
+
+// Lane 0: the first class, starting at `home`, that has a published request
+// at its head (seen from the request's device copy when there is one, else
+// from the class tail), or -1.
+__device__ __forceinline__ int serve_pick(const ServeArgs& s, int home) {
+  for (int j = 0; j < kWarpClasses; ++j) {
+    const int c = home + j < kWarpClasses ? home + j : home + j - kWarpClasses;
+    const unsigned long long head = volatile_load(&s.class_head[c]);
+    const ServeMirror* m = s.mirror + unsigned(c) * unsigned(s.cap) + unsigned(head % unsigned(s.cap));
+    if (volatile_load(&m->seq) == head + 1) return c;
+    if (head < load_acquire_sys(&s.ctrl->class_tail[c])) return c;
+  }
+  return -1;
+}
+
+// Each warp serves its home class (warps are spread evenly over the classes)
+// while that class has work, and otherwise the next class in turn that has
+// some, so a request can use every warp of the grid when the others are
+// idle. A class body returns as soon as its class has nothing left to hand
+// out. Idle warps read the published-request total (one word of mapped host
+// memory) and look at the class tails only when it has moved; they exit
+// after idle_ns without work or on the stop flag. s.cls is the liveness
+// counter of this kernel.
+template <int EL, bool X3>
+__global__ void __launch_bounds__(kServeThreads, 1)
+    warp_serve_kernel(const __grid_constant__ ServeWarpArgs p) {
+  const ServeArgs& s = p.k;
+  const int lane = threadIdx.x & 31;
+  unsigned char* mine = warp_slice<kServeSlice>();
+  if (lane == 0) serve_unit_enter(s);
+  const int home = int((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kWarpClasses);
+  unsigned long long t_idle = global_timer_ns(), seen = ~0ull;
+  unsigned sleep_ns = 128;
+  while (true) {
+    int pick = -1;
+    if (lane == 0) {
+      if (volatile_load(&s.ctrl->stop)) {
+        pick = -2;
+      } else {
+        const unsigned long long total = load_acquire_sys(&s.ctrl->class_tail[kServeTotal]);
+        if (total != seen) {
+          pick = serve_pick(s, home);
+          if (pick < 0) seen = total;  // nothing new until the total moves
+        }
+        if (pick == -1) {
+          if (global_timer_ns() - t_idle > s.idle_ns) {
+            pick = -2;
+          } else {
+            __nanosleep(sleep_ns);
+            sleep_ns = sleep_ns < 2048 ? 2 * sleep_ns : 2048;
+          }
+        }
+      }
+    }
+    pick = __shfl_sync(0xffffffffu, pick, 0);
+    if (pick == -2) break;
+    if (pick < 0) continue;
+    serve_class<EL, X3>(pick, p, mine);
+    t_idle = global_timer_ns();
+    sleep_ns = 128;
+    seen = ~0ull;
+  }
+  if (lane == 0) serve_unit_exit(s);
 }
 
 }  // namespace cgm

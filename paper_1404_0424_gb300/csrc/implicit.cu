@@ -54,7 +54,7 @@ cudaError_t det(const DetectArgs& a, cudaStream_t s) {
   constexpr int NTHR = TileCfg<UT>::NTHR;
   const uint32_t smem = implicit_plan<UT>(a.B, a.U, a.R, true).total;
   int grid = 0;
-  cudaError_t err = launch_one(detect_implicit_kernel<UT>, 0x10 | UT, NTHR, smem, a.n_inst, &grid);
+  cudaError_t err = launch_one(detect_implicit_kernel<UT>, 0x100 | UT, NTHR, smem, a.n_inst, &grid);
   if (err != cudaSuccess) return err;
   detect_implicit_kernel<UT><<<unsigned(grid), NTHR, smem, s>>>(a);
   return cudaGetLastError();
@@ -65,7 +65,7 @@ cudaError_t pre(const PrecodeArgs& a, cudaStream_t s) {
   constexpr int NTHR = TileCfg<UT>::NTHR;
   const uint32_t smem = implicit_plan<UT>(a.B, a.U, a.R, false).total;
   int grid = 0;
-  cudaError_t err = launch_one(precode_implicit_kernel<UT>, 0x20 | UT, NTHR, smem, a.n_inst, &grid);
+  cudaError_t err = launch_one(precode_implicit_kernel<UT>, 0x200 | UT, NTHR, smem, a.n_inst, &grid);
   if (err != cudaSuccess) return err;
   precode_implicit_kernel<UT><<<unsigned(grid), NTHR, smem, s>>>(a);
   return cudaGetLastError();

@@ -17,8 +17,22 @@ inline int padded_users(int U) { return U <= 4 ? 4 : U <= 8 ? 8 : U <= 16 ? 16 :
 struct DeviceInfo {
   int sm_count = 0;
   int smem_optin = 0;
+  int smem_per_sm = 0;        // shared memory of one SM
+  int smem_reserved = 0;      // shared memory the system reserves per resident block
 };
 int device_info(DeviceInfo* out);
+
+// Serving kernels hold their SMs for as long as they have work, and the
+// class kernels start and stop independently. If their CTAs had different
+// footprints, a relaunched class could find every SM partly filled and none
+// with room for one of its CTAs; the block scheduler would then hold back
+// every grid launched after it as well. So every serving CTA is padded to
+// more than half an SM's shared memory (one CTA per SM, whatever its class),
+// and the class grids together hold at most one CTA per SM.
+inline uint32_t serve_smem(const DeviceInfo& d, uint32_t need) {
+  const uint32_t floor = uint32_t(d.smem_per_sm / 2 - d.smem_reserved + 16);
+  return need > floor ? need : floor;
+}
 
 // Launchers (defined in detect.cu / precode.cu). Return cudaError_t values.
 cudaError_t launch_detect(int UT, const DetectArgs& a, cudaStream_t s, int* grid_out);
@@ -38,19 +52,21 @@ cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const Ba
                             int max_grid, cudaStream_t s, bool launch, uint32_t* smem_out,
                             int* grid_out);
 
-// Serving kernels (tc.cu): one persistent kernel per (operation, UT). With
-// launch = false only the shared-memory size and resident CTAs are computed.
+// CTA serving kernels (tc.cu), used for exact-tracker detection: one
+// persistent kernel per (operation, UT). With launch = false only the
+// shared-memory size and resident CTAs are computed.
 cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
                             cudaStream_t st, bool launch, uint32_t* smem_out, int* resident_out);
 
-// Warp-per-instance kernels (warp.cu): padded users 8 or 16, approximate
+// Warp-per-instance kernels (warp.cu): padded users 8, 16 or 32, approximate
 // tracker only. Batch and serve forms as above (grid in CTAs of 4 warps).
 cudaError_t launch_detect_warp(int UT, int el, bool x3, const DetectArgs& a, cudaStream_t s);
 cudaError_t launch_precode_warp(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s);
 cudaError_t launch_batch_warp(int op, int UT, int el, bool x3, const BatchArgs& b, int max_grid,
                               cudaStream_t s, bool launch, int* grid_out);
-cudaError_t launch_serve_warp(int op, int UT, int el, bool x3, const ServeArgs& sa, int grid,
-                              cudaStream_t s, bool launch, int* resident_out);
+// The serving kernel of the six approximate-tracker classes (warp_serve_kernel).
+cudaError_t launch_serve_warp(int el, bool x3, const ServeArgs& sa, int grid, cudaStream_t s,
+                              bool launch, int* resident_out);
 
 // Implicit-product FP32 kernels (implicit.cu): e = H^H (H p) + sigma p.
 cudaError_t launch_detect_implicit(int UT, const DetectArgs& a, cudaStream_t s);

@@ -1,13 +1,19 @@
-// Host side of the serving loop behind cg_serve_*: ring slots, admission by
-// HBM budget, stream-ordered publication into device memory (no host wait),
-// on-demand launch of the persistent class kernels (liveness read from
-// mapped memory, no CUDA call), completion polling and bounded shutdown.
+// Host side of the serving loop behind cg_serve_*: slots from a free list,
+// admission by HBM budget, publication through mapped host memory with no
+// CUDA call (a submit is a few stores and a release fence), on-demand launch
+// of the two persistent serving kernels (one for the six approximate-tracker
+// classes, one for exact-tracker detection; liveness read from mapped
+// memory), completion polling and bounded shutdown.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstring>
 #include <ctime>
+#include <deque>
 #include <mutex>
 #include <thread>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "cgmimo.h"
@@ -18,7 +24,16 @@ using namespace cgm;
 
 namespace {
 
-constexpr int kClasses = 6;  // (detect, precode) x (UT 8, 16, 32)
+// (detect, precode) x (UT 8, 16, 32) on the warp-per-instance serving kernel,
+// and exact-tracker detection on the CTA kernel (32 padded users)
+constexpr int kClasses = 7;
+constexpr int kExactClass = 6;
+constexpr int kRingPerSlot = 4;   // class ring positions per slot (ring = 4 x capacity)
+// Serving kernels: 0 serves classes 0-5, 1 the exact class. A kernel's
+// liveness counters in the control block are those of its ServeArgs::cls.
+constexpr int kKernels = 2;
+int kernel_of(int cls) { return cls == kExactClass ? 1 : 0; }
+int live_index(int k) { return k == 0 ? 0 : kExactClass; }
 
 int64_t mono_ns() {
   timespec ts;
@@ -26,15 +41,19 @@ int64_t mono_ns() {
   return int64_t(ts.tv_sec) * 1000000000LL + ts.tv_nsec;
 }
 
-// Class of a request: (operation, padded users 8 / 16 / 32). Detection with
-// the exact tracker runs in the (detect, 32) class, whose CTA kernel has the
-// shared memory for it; the 8- and 16-user classes run one warp per instance.
+// Class of a request: (operation, padded users 8 / 16 / 32), one warp per
+// instance; detection with the exact tracker has a class of its own whose
+// CTA kernel has the shared memory for the U x U recursion of Eq. 10.
 int class_of(const cg_desc& d, int* UT) {
   const int pu = padded_users(d.U);
   *UT = pu < 8 ? 8 : pu;
-  if (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT) *UT = 32;
+  if (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT) {
+    *UT = 32;
+    return kExactClass;
+  }
   return d.op * 3 + (*UT == 8 ? 0 : *UT == 16 ? 1 : 2);
 }
+
 
 int64_t footprint(const cg_desc& d) {
   const int64_t n = d.n_inst, B = d.B, U = d.U, R = d.R, q = d.qam_bits;
@@ -48,8 +67,8 @@ struct SlotInfo {
   int64_t bytes = 0;
   int64_t submit_ns = 0;
   int64_t complete_ns = 0;
+  bool in_use = false;   // holds a request that a poll has not yet reported done
   bool released = true;  // its bytes no longer count against the budget
-  bool reaped = true;    // a poll has reported it done: the slot may be reused
 };
 
 }  // namespace
@@ -59,101 +78,115 @@ struct cg_server {
   cg_serve_cfg cfg{};
   int el = 1;
   bool x3 = true;
-  // device memory: slot records, class heads, class tails, class rings
+  int cap = 0, ring = 0;
+  // device memory: per-slot progress counters, class heads
   void* dmem = nullptr;
-  ServeSlot* d_slots = nullptr;
+  ServeCount* d_counts = nullptr;
+  ServeMirror* d_mirror = nullptr;
   unsigned long long* d_head = nullptr;
-  unsigned long long* d_tail = nullptr;
-  unsigned long long* d_ring = nullptr;
-  // pinned staging of the asynchronous copies that publish a request
-  void* smem_host = nullptr;
-  ServeSlot* st_slot = nullptr;          // [cap] slot records
-  unsigned long long* st_ring = nullptr;  // [classes][cap] ring entries
-  unsigned long long* st_tail = nullptr;  // [cap] class tail published with each ticket
-  // mapped host memory: control block and completion records
+  // mapped host memory: control block, completions, descriptors, class rings
   void* hmem = nullptr;
   ServeCtrl* h_ctrl = nullptr;
   ServeCompletion* h_comp = nullptr;
+  ServeDesc* h_desc = nullptr;
+  ServeEntry* h_ring = nullptr;
   ServeCtrl* d_ctrl = nullptr;
   ServeCompletion* d_comp = nullptr;
-  cudaStream_t ks[kClasses] = {};
-  cudaStream_t cs = nullptr;
-  unsigned long long launched_gen[kClasses] = {};
-  int grid[kClasses] = {};
+  ServeDesc* d_desc = nullptr;
+  ServeEntry* d_ring = nullptr;
+  cudaStream_t ks[kKernels] = {};
+  unsigned long long launched_gen[kKernels] = {};
+  int grid[kKernels] = {};
   std::mutex mu;
-  uint64_t next = 0, head = 0;
+  uint64_t next = 0;                                 // next ticket
   uint64_t published[kClasses] = {};
-  std::vector<SlotInfo> info;
-  int64_t inflight = 0;
+  uint64_t published_total = 0;
+  std::deque<std::pair<uint64_t, int>> queued[kClasses];  // (ticket, slot) not yet seen complete
+  std::vector<int> free_slots;
+  std::vector<SlotInfo> info;                        // per slot
+  std::unordered_map<uint64_t, int> ticket_slot;     // slot of each ticket that holds one
+  int64_t inflight = 0;                              // budget bytes of unfinished requests
 };
 
 namespace {
 
-ServeArgs args_for(const cg_server* s, int cls) {
+ServeArgs args_for(const cg_server* s, int k) {
   ServeArgs a{};
-  a.slots = s->d_slots;
+  a.counts = s->d_counts;
+  a.mirror = s->d_mirror;
+  a.descs = s->d_desc;
   a.class_ring = s->d_ring;
-  a.class_tail = s->d_tail;
   a.ctrl = s->d_ctrl;
   a.comp = s->d_comp;
   a.class_head = s->d_head;
-  a.cls = cls;
-  a.cap = s->cfg.capacity;
+  a.cls = live_index(k);
+  a.cap = s->ring;
   a.PB = s->cfg.max_B;
   a.PR = s->cfg.max_R;
-  a.PEX = cls == 2 ? 1 : 0;
+  a.PEX = k == 1 ? 1 : 0;
   a.idle_ns = (unsigned long long)s->cfg.idle_timeout_ms * 1000000ull;
-  a.gen = s->launched_gen[cls];
+  a.gen = s->launched_gen[k];
   return a;
 }
 
-int class_ut(int cls) { return cls % 3 == 0 ? 8 : cls % 3 == 1 ? 16 : 32; }
+// Launches serving kernel k (or, with launch = false, reports its resident CTAs).
+cudaError_t launch_kernel(const cg_server* s, int k, bool launch, int* resident) {
+  const ServeArgs a = args_for(s, k);
+  if (k == 0) return launch_serve_warp(s->el, s->x3, a, s->grid[0], s->ks[0], launch, resident);
+  return launch_serve_tc(CG_OP_DETECT, 32, s->el, s->x3, a, s->grid[1], s->ks[1], launch, nullptr,
+                         resident);
+}
 
-// Launches the class kernel unless a launch of it is still alive: the last
-// work unit of launch generation g to exit writes g into the mapped control
-// block, so the check is a memory read. A relaunch queues on the class
-// stream behind a launch that is just finishing.
+// Launches the serving kernel of a class unless a launch of it is still
+// alive: the last work unit of launch generation g to exit writes g into the
+// mapped control block, so the check is a memory read. A relaunch queues on
+// the kernel's stream behind a launch that is just finishing.
 int ensure_running(cg_server* s, int cls) {
+  const int k = kernel_of(cls);
   const auto* ex = reinterpret_cast<const std::atomic<unsigned long long>*>(
-      &s->h_ctrl->exited_gen[cls]);
-  if (s->launched_gen[cls] > ex->load(std::memory_order_acquire)) return CG_OK;
-  ++s->launched_gen[cls];
-  const cudaError_t err = launch_serve_tc(cls / 3, class_ut(cls), s->el, s->x3, args_for(s, cls),
-                                          s->grid[cls], s->ks[cls], true, nullptr, nullptr);
-  if (err != cudaSuccess) {
-    --s->launched_gen[cls];
+      &s->h_ctrl->exited_gen[live_index(k)]);
+  if (s->launched_gen[k] > ex->load(std::memory_order_acquire)) return CG_OK;
+  ++s->launched_gen[k];
+  if (launch_kernel(s, k, true, nullptr) != cudaSuccess) {
+    --s->launched_gen[k];
     return CG_ECUDA;
   }
   return CG_OK;
 }
 
-bool complete(const cg_server* s, uint64_t ticket) {
-  const ServeCompletion* c = s->h_comp + ticket % uint64_t(s->cfg.capacity);
-  const auto* seq = reinterpret_cast<const std::atomic<unsigned long long>*>(&c->seq);
+bool complete(const cg_server* s, uint64_t ticket, int slot) {
+  const auto* seq =
+      reinterpret_cast<const std::atomic<unsigned long long>*>(&s->h_comp[slot].seq);
   return seq->load(std::memory_order_acquire) == ticket + 1;
 }
 
-// Releases the budget bytes of every completed request, then frees the
-// ring slots at the head whose requests a poll has reported done.
+// Releases the budget bytes of completed requests and drops completed
+// requests from the front of the class queues (a class ring position is
+// reused only after its request is complete, hence fully handed out).
 void retire(cg_server* s) {
-  const uint64_t cap = uint64_t(s->cfg.capacity);
-  for (uint64_t t = s->head; t < s->next; ++t) {
-    SlotInfo& in = s->info[t % cap];
-    if (!in.released && complete(s, t)) {
+  for (int sl = 0; sl < s->cap; ++sl) {
+    SlotInfo& in = s->info[sl];
+    if (in.in_use && !in.released && complete(s, in.ticket, sl)) {
       s->inflight -= in.bytes;
       in.released = true;
     }
   }
-  while (s->head < s->next && s->info[s->head % cap].reaped) ++s->head;
+  for (int c = 0; c < kClasses; ++c) {
+    auto& q = s->queued[c];
+    while (!q.empty()) {
+      const uint64_t t = q.front().first;
+      const int sl = q.front().second;
+      if (s->info[sl].ticket == t && !complete(s, t, sl)) break;
+      q.pop_front();
+    }
+  }
 }
 
 void destroy_server(cg_server* s) {
-  for (int c = 0; c < kClasses; ++c)
-    if (s->ks[c]) cudaStreamDestroy(s->ks[c]);
-  if (s->cs) cudaStreamDestroy(s->cs);
+  for (int k = 0; k < kKernels; ++k)
+    if (s->ks[k]) cudaStreamDestroy(s->ks[k]);
   if (s->dmem) cudaFree(s->dmem);
   if (s->hmem) cudaFreeHost(s->hmem);
-  if (s->smem_host) cudaFreeHost(s->smem_host);
   delete s;
 }
 
@@ -165,7 +198,7 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
   if (cfg == nullptr || out == nullptr) return CG_EINVAL;
   *out = nullptr;
   const cg_serve_cfg c = *cfg;
-  if (c.capacity < 1 || c.capacity > (1 << 20)) return CG_EINVAL;
+  if (c.capacity < 1 || c.capacity > (1 << 14)) return CG_EINVAL;
   if (c.precision < CG_PREC_BF16 || c.precision > CG_PREC_FP16X3) return CG_EINVAL;
   if (c.hbm_budget_bytes <= 0) return CG_EINVAL;
   if (c.max_B < 1 || c.max_B > CG_B_MAX || c.max_R < 1 || c.max_R > CG_R_MAX) return CG_EINVAL;
@@ -175,22 +208,24 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
   s->cfg = c;
   s->el = (c.precision == CG_PREC_BF16 || c.precision == CG_PREC_BF16X3) ? 0 : 1;
   s->x3 = c.precision == CG_PREC_BF16X3 || c.precision == CG_PREC_FP16X3;
-  s->info.resize(size_t(c.capacity));
+  s->cap = c.capacity;
+  s->ring = kRingPerSlot * c.capacity;
+  s->info.resize(size_t(s->cap));
+  s->ticket_slot.reserve(size_t(s->cap) * 2);
+  for (int sl = s->cap - 1; sl >= 0; --sl) s->free_slots.push_back(sl);
   if (cudaGetDevice(&s->dev) != cudaSuccess) {
     delete s;
     return CG_ECUDA;
   }
-  const size_t cap = size_t(c.capacity);
-  const size_t u64 = sizeof(unsigned long long);
-  const size_t head_off = sizeof(ServeSlot) * cap;
-  const size_t tail_off = head_off + u64 * 8;
-  const size_t ring_off = tail_off + u64 * 8;
-  const size_t dbytes = ring_off + u64 * kClasses * cap;
+  const size_t cap = size_t(s->cap);
+  const size_t positions = size_t(kClasses) * size_t(s->ring);
+  const size_t mirror_off = (sizeof(ServeCount) * positions + 255) & ~size_t(255);
+  const size_t head_off = mirror_off + sizeof(ServeMirror) * positions;
+  const size_t dbytes = head_off + sizeof(unsigned long long) * 8;
   const size_t comp_off = (sizeof(ServeCtrl) + 255) & ~size_t(255);
-  const size_t hbytes = comp_off + sizeof(ServeCompletion) * cap;
-  const size_t st_ring_off = sizeof(ServeSlot) * cap;
-  const size_t st_tail_off = st_ring_off + u64 * kClasses * cap;
-  const size_t sbytes = st_tail_off + u64 * cap;
+  const size_t desc_off = comp_off + sizeof(ServeCompletion) * cap;
+  const size_t ring_off = desc_off + sizeof(ServeDesc) * cap;
+  const size_t hbytes = ring_off + sizeof(ServeEntry) * kClasses * size_t(s->ring);
   int rc = CG_OK;
   if (cudaMalloc(&s->dmem, dbytes) != cudaSuccess) {
     s->dmem = nullptr;
@@ -200,54 +235,50 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
     s->hmem = nullptr;
     rc = CG_ENOMEM;
   }
-  if (rc == CG_OK && cudaHostAlloc(&s->smem_host, sbytes, cudaHostAllocDefault) != cudaSuccess) {
-    s->smem_host = nullptr;
-    rc = CG_ENOMEM;
-  }
   if (rc == CG_OK) {
     std::memset(s->hmem, 0, hbytes);
-    std::memset(s->smem_host, 0, sbytes);
     char* dm = static_cast<char*>(s->dmem);
-    s->d_slots = reinterpret_cast<ServeSlot*>(dm);
+    s->d_counts = reinterpret_cast<ServeCount*>(dm);
+    s->d_mirror = reinterpret_cast<ServeMirror*>(dm + mirror_off);
     s->d_head = reinterpret_cast<unsigned long long*>(dm + head_off);
-    s->d_tail = reinterpret_cast<unsigned long long*>(dm + tail_off);
-    s->d_ring = reinterpret_cast<unsigned long long*>(dm + ring_off);
-    char* st = static_cast<char*>(s->smem_host);
-    s->st_slot = reinterpret_cast<ServeSlot*>(st);
-    s->st_ring = reinterpret_cast<unsigned long long*>(st + st_ring_off);
-    s->st_tail = reinterpret_cast<unsigned long long*>(st + st_tail_off);
     char* h = static_cast<char*>(s->hmem);
     s->h_ctrl = reinterpret_cast<ServeCtrl*>(h);
     s->h_comp = reinterpret_cast<ServeCompletion*>(h + comp_off);
+    s->h_desc = reinterpret_cast<ServeDesc*>(h + desc_off);
+    s->h_ring = reinterpret_cast<ServeEntry*>(h + ring_off);
     void* dv = nullptr;
     if (cudaHostGetDevicePointer(&dv, s->hmem, 0) != cudaSuccess) rc = CG_ECUDA;
     char* d = static_cast<char*>(dv);
     s->d_ctrl = reinterpret_cast<ServeCtrl*>(d);
     s->d_comp = reinterpret_cast<ServeCompletion*>(d + comp_off);
+    s->d_desc = reinterpret_cast<ServeDesc*>(d + desc_off);
+    s->d_ring = reinterpret_cast<ServeEntry*>(d + ring_off);
   }
-  if (rc == CG_OK && cudaMemset(s->dmem, 0, dbytes) != cudaSuccess) rc = CG_ECUDA;
-  for (int k = 0; k < kClasses && rc == CG_OK; ++k)
-    if (cudaStreamCreateWithFlags(&s->ks[k], cudaStreamNonBlocking) != cudaSuccess) rc = CG_ECUDA;
-  if (rc == CG_OK && cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess)
+  if (rc == CG_OK && (cudaMemset(s->dmem, 0, dbytes) != cudaSuccess ||
+                      cudaDeviceSynchronize() != cudaSuccess))
     rc = CG_ECUDA;
-  // launch shapes: each class gets a share of the SMs in proportion to the
-  // cost of one of its instances (weights 1, 2, 8 for 8, 16, 32 padded
-  // users), as many work units as are resident on that share
+  for (int k = 0; k < kKernels && rc == CG_OK; ++k)
+    if (cudaStreamCreateWithFlags(&s->ks[k], cudaStreamNonBlocking) != cudaSuccess) rc = CG_ECUDA;
+  // launch shapes: every serving CTA fills one SM (its shared memory is
+  // padded past half an SM). The exact-tracker kernel has 1/16 of the SMs and
+  // the warp kernel the rest, so either one, relaunched while the other runs,
+  // finds SMs free for all of its CTAs.
   DeviceInfo di;
   if (rc == CG_OK && device_info(&di) != 0) rc = CG_ECUDA;
-  const double weight[3] = {1.0, 2.0, 8.0};
-  const double wsum = 2.0 * (weight[0] + weight[1] + weight[2]);
-  for (int k = 0; k < kClasses && rc == CG_OK; ++k) {
-    uint32_t smem = 0;
+  if (rc == CG_OK) {
+    const int exact = std::max(1, di.sm_count / 16);
+    s->grid[1] = exact;
+    s->grid[0] = di.sm_count - exact;
+    if (c.ctas_per_class > 0)
+      for (int k = 0; k < kKernels; ++k) s->grid[k] = std::min(s->grid[k], c.ctas_per_class);
+  }
+  for (int k = 0; k < kKernels && rc == CG_OK; ++k) {
     int resident = 0;
-    const cudaError_t err = launch_serve_tc(k / 3, class_ut(k), s->el, s->x3, args_for(s, k), 0,
-                                            nullptr, false, &smem, &resident);
-    if (err != cudaSuccess) {
+    const cudaError_t err = launch_kernel(s, k, false, &resident);
+    if (err != cudaSuccess)
       rc = err == cudaErrorInvalidValue ? CG_EINVAL : CG_ECUDA;
-      break;
-    }
-    const int share = int(double(resident) * weight[k % 3] / wsum + 0.5);
-    s->grid[k] = c.ctas_per_class > 0 ? c.ctas_per_class : (share > 0 ? share : 1);
+    else if (resident > di.sm_count)  // the padding did not make it one CTA per SM
+      rc = CG_ECUDA;
   }
   if (rc != CG_OK) {
     destroy_server(s);
@@ -282,51 +313,47 @@ int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket) {
   if (rc != CG_OK) return rc;
   const int64_t bytes = footprint(d);
   if (bytes > s->cfg.hbm_budget_bytes) return CG_ETOOBIG;
-  if (uint64_t(d.n_inst) > SERVE_NINST_MASK) return CG_ETOOBIG;
+  if (d.n_inst >= (int64_t(1) << 24)) return CG_ETOOBIG;  // 24-bit instance counts
   std::lock_guard<std::mutex> lk(s->mu);
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != s->dev) return CG_EINVAL;
   retire(s);
-  const uint64_t cap = uint64_t(s->cfg.capacity);
-  if (s->next - s->head >= cap) return CG_EAGAIN;
-  if (s->inflight + bytes > s->cfg.hbm_budget_bytes) return CG_EAGAIN;
   int UT;
   const int cls = class_of(d, &UT);
-  const uint64_t t = s->next;
-  const uint64_t slot = t % cap;
-  if (t >> (64 - SERVE_NINST_BITS)) return CG_ETOOBIG;  // ticket space exhausted
-  // publication: the slot record, the class ring entry and the new class
-  // tail are copied in that order on one stream, so the device sees the
-  // tail only after the record and the entry have landed. Each copy reads
-  // its own pinned staging word (records and tails per slot, entries per
-  // ring position), which stays unchanged until the copy has run.
-  ServeSlot& rec = s->st_slot[slot];
-  rec = ServeSlot{};
-  rec.d = d;
-  rec.ticket = t;
-  rec.claim = (t & 0xffffffffull) << 32;
+  if (s->free_slots.empty()) return CG_EAGAIN;
+  if (s->inflight + bytes > s->cfg.hbm_budget_bytes) return CG_EAGAIN;
+  if (s->queued[cls].size() >= size_t(s->ring)) return CG_EAGAIN;
+  const int slot = s->free_slots.back();
+  s->free_slots.pop_back();
+  if (s->info[slot].ticket != ~0ull) s->ticket_slot.erase(s->info[slot].ticket);
+  const uint64_t t = s->next++;
+  // publication: descriptor, completion record and ring entry first, then
+  // (release) the class tail that makes them visible to the class kernel
+  ServeDesc& ds = s->h_desc[slot];
+  ds.d = d;
+  ds.ticket = t;
   std::memset(&s->h_comp[slot], 0, sizeof(ServeCompletion));
-  const size_t pos = size_t(cls) * cap + size_t(s->published[cls] % cap);
-  s->st_ring[pos] = (t << SERVE_NINST_BITS) | uint64_t(d.n_inst);
-  s->st_tail[slot] = s->published[cls] + 1;
-  if (cudaMemcpyAsync(s->d_slots + slot, &rec, sizeof(rec), cudaMemcpyHostToDevice, s->cs) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(s->d_ring + pos, &s->st_ring[pos], sizeof(unsigned long long),
-                      cudaMemcpyHostToDevice, s->cs) != cudaSuccess ||
-      cudaMemcpyAsync(s->d_tail + cls, &s->st_tail[slot], sizeof(unsigned long long),
-                      cudaMemcpyHostToDevice, s->cs) != cudaSuccess)
-    return CG_ECUDA;
+  ServeEntry& e = s->h_ring[size_t(cls) * s->ring + size_t(s->published[cls] % s->ring)];
+  e.slot_ninst = (uint64_t(slot) << 32) | uint64_t(d.n_inst);
+  e.ticket = t;
   ++s->published[cls];
+  ++s->published_total;
+  std::atomic_thread_fence(std::memory_order_release);
+  reinterpret_cast<std::atomic<unsigned long long>*>(&s->h_ctrl->class_tail[cls])
+      ->store(s->published[cls], std::memory_order_release);
+  reinterpret_cast<std::atomic<unsigned long long>*>(&s->h_ctrl->class_tail[kServeTotal])
+      ->store(s->published_total, std::memory_order_release);
   SlotInfo& in = s->info[slot];
   in.ticket = t;
   in.cls = cls;
   in.bytes = bytes;
   in.submit_ns = mono_ns();
   in.complete_ns = 0;
+  in.in_use = true;
   in.released = false;
-  in.reaped = false;
   s->inflight += bytes;
-  s->next = t + 1;
+  s->queued[cls].emplace_back(t, slot);
+  s->ticket_slot[t] = slot;
   *ticket = t;
   return ensure_running(s, cls);
 }
@@ -334,15 +361,16 @@ int cg_serve_submit(cg_server* s, const cg_desc* req, uint64_t* ticket) {
 int cg_serve_poll(cg_server* s, uint64_t ticket, int32_t* done, cg_req_stats* stats) {
   if (s == nullptr || done == nullptr) return CG_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
-  const uint64_t cap = uint64_t(s->cfg.capacity);
-  SlotInfo& in = s->info[ticket % cap];
-  if (ticket >= s->next || in.ticket != ticket) return CG_EINVAL;
-  *done = complete(s, ticket) ? 1 : 0;
+  if (ticket >= s->next) return CG_EINVAL;
+  const auto found = s->ticket_slot.find(ticket);
+  if (found == s->ticket_slot.end()) return CG_EINVAL;  // its slot serves a later request now
+  const int slot = found->second;
+  SlotInfo& in = s->info[slot];
+  *done = (!in.in_use || complete(s, ticket, slot)) ? 1 : 0;
   if (*done) {
     if (in.complete_ns == 0) in.complete_ns = mono_ns();
-    in.reaped = true;
     if (stats) {
-      const ServeCompletion* c = s->h_comp + ticket % cap;
+      const ServeCompletion* c = s->h_comp + slot;
       stats->status = c->status;
       stats->pad = 0;
       stats->submit_ns = in.submit_ns;
@@ -350,7 +378,14 @@ int cg_serve_poll(cg_server* s, uint64_t ticket, int32_t* done, cg_req_stats* st
       stats->device_first_ns = int64_t(c->t_first_ns);
       stats->device_done_ns = int64_t(c->t_done_ns);
     }
-    retire(s);
+    if (in.in_use) {  // first report of done: the slot becomes free
+      if (!in.released) {
+        s->inflight -= in.bytes;
+        in.released = true;
+      }
+      in.in_use = false;
+      s->free_slots.push_back(slot);
+    }
     return CG_OK;
   }
   // not done: make sure its class kernel is alive (it may have idled out just
@@ -365,7 +400,7 @@ int cg_serve_destroy(cg_server* s) {
     reinterpret_cast<std::atomic<int>*>(&s->h_ctrl->stop)->store(1, std::memory_order_release);
   }
   const auto t0 = std::chrono::steady_clock::now();
-  for (int k = 0; k < kClasses; ++k) {
+  for (int k = 0; k < kKernels; ++k) {
     while (s->launched_gen[k] > 0) {
       const cudaError_t q = cudaStreamQuery(s->ks[k]);
       if (q != cudaErrorNotReady) break;
@@ -373,7 +408,6 @@ int cg_serve_destroy(cg_server* s) {
       std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
   }
-  if (cudaStreamSynchronize(s->cs) != cudaSuccess) return CG_ECUDA;
   destroy_server(s);
   return CG_OK;
 }

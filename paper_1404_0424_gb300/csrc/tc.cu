@@ -198,7 +198,7 @@ cudaError_t batch_ut(int op, int el, bool x3, bool full, const BatchArgs& b, int
 cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const BatchArgs& b,
                             int max_grid, cudaStream_t s, bool launch, uint32_t* smem_out,
                             int* grid_out) {
-  if (UT <= 16 && b.PEX == 0) {  // warp-per-instance kernels
+  if (b.PEX == 0) {  // warp-per-instance kernels
     if (smem_out) *smem_out = 0;
     return launch_batch_warp(op, UT, el, x3, b, max_grid, s, launch, grid_out);
   }
@@ -225,8 +225,11 @@ template <int UT, int EL, bool X3>
 cudaError_t serve_t(int op, const ServeArgs& s, int grid, cudaStream_t st, bool launch,
                     uint32_t* smem_out, int* resident_out) {
   constexpr int NTHR = TcCfg<UT>::NTHR;
-  const uint32_t smem = op == 0 ? tc_detect_plan<UT>(s.PB, UT, s.PR, s.PEX).total
-                                : tc_precode_plan<UT>(s.PB, UT, s.PR).total;
+  DeviceInfo di;
+  if (device_info(&di) != 0) return cudaErrorUnknown;
+  // padded to one CTA per SM like every serving CTA
+  const uint32_t smem = serve_smem(di, op == 0 ? tc_detect_plan<UT>(s.PB, UT, s.PR, s.PEX).total
+                                               : tc_precode_plan<UT>(s.PB, UT, s.PR).total);
   int slots = 0;
   const uint64_t id = (op == 0 ? 0x10000 : 0x20000) | (UT << 3) | (EL << 2) | (X3 ? 2 : 0);
   cudaError_t err = op == 0 ? prepare(detect_tc_serve_kernel<UT, EL, X3>, id, NTHR, smem, &slots)
@@ -256,10 +259,6 @@ cudaError_t serve_ut(int op, int el, bool x3, const ServeArgs& s, int grid, cuda
 
 cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
                             cudaStream_t st, bool launch, uint32_t* smem_out, int* resident_out) {
-  if (UT <= 16 && s.PEX == 0) {  // warp-per-instance kernels
-    if (smem_out) *smem_out = 0;
-    return launch_serve_warp(op, UT, el, x3, s, grid, st, launch, resident_out);
-  }
   switch (UT) {
     case 8: return serve_ut<8>(op, el, x3, s, grid, st, launch, smem_out, resident_out);
     case 16: return serve_ut<16>(op, el, x3, s, grid, st, launch, smem_out, resident_out);

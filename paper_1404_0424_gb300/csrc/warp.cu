@@ -1,5 +1,5 @@
-// Launchers of the warp-per-instance tensor-core kernels (padded users 8 or
-// 16, approximate SINR tracker): single calls, plan bins and serving classes.
+// Launchers of the warp-per-instance tensor-core kernels (padded users 8, 16
+// or 32, approximate SINR tracker): single calls, plan bins and serving classes.
 #include <mutex>
 #include <unordered_map>
 
@@ -15,7 +15,8 @@ std::unordered_map<uint64_t, int> g_occ;  // (device, kernel id) -> resident CTA
 
 // Resident CTAs of `kern` on the current device (all SMs).
 template <typename Kern>
-cudaError_t resident_ctas(Kern kern, uint64_t id, uint32_t smem, int* out) {
+cudaError_t resident_ctas(Kern kern, uint64_t id, uint32_t smem, int* out,
+                          int threads = WarpCfg<8>::NTHR) {
   DeviceInfo di;
   if (device_info(&di) != 0) return cudaErrorUnknown;
   int dev = 0;
@@ -29,7 +30,7 @@ cudaError_t resident_ctas(Kern kern, uint64_t id, uint32_t smem, int* out) {
     if (int(smem) > di.smem_optin) return cudaErrorInvalidValue;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (err != cudaSuccess) return err;
     if (occ < 1) occ = 1;
     g_occ[key] = occ;
@@ -91,21 +92,26 @@ cudaError_t batch(int op, const BatchArgs& b, int max_grid, cudaStream_t s, bool
   return cudaGetLastError();
 }
 
-template <int UT, int EL, bool X3>
-cudaError_t serve(int op, const ServeArgs& sa, int grid, cudaStream_t s, bool launch,
-                  int* resident_out) {
-  const uint32_t smem = op == 0 ? WarpCfg<UT>::SMEM : WarpCfg<UT>::PRE_SMEM;
+template <int EL, bool X3>
+cudaError_t serve(const ServeArgs& sa, int grid, cudaStream_t s, bool launch, int* resident_out) {
+  DeviceInfo di;
+  if (device_info(&di) != 0) return cudaErrorUnknown;
+  // a slice for the largest class per warp, padded to one CTA per SM
+  const uint32_t smem = serve_smem(di, uint32_t(kServeThreads / 32) * kServeSlice);
   int res = 0;
-  const uint64_t id = (op == 0 ? 0x1000 : 0x2000) | (UT << 2) | (EL << 1) | (X3 ? 1 : 0);
-  cudaError_t err = op == 0 ? resident_ctas(detect_warp_serve_kernel<UT, EL, X3>, id, smem, &res)
-                            : resident_ctas(precode_warp_serve_kernel<UT, EL, X3>, id, smem, &res);
+  const uint64_t id = 0x4000 | (EL << 1) | (X3 ? 1 : 0);
+  cudaError_t err = resident_ctas(warp_serve_kernel<EL, X3>, id, smem, &res, kServeThreads);
   if (err != cudaSuccess) return err;
   if (resident_out) *resident_out = res;
   if (!launch) return cudaSuccess;
-  if (op == 0)
-    detect_warp_serve_kernel<UT, EL, X3><<<unsigned(grid), WarpCfg<UT>::NTHR, smem, s>>>(sa);
-  else
-    precode_warp_serve_kernel<UT, EL, X3><<<unsigned(grid), WarpCfg<UT>::NTHR, smem, s>>>(sa);
+  ServeWarpArgs p;
+  p.k = sa;
+  for (int c = 0; c < kWarpClasses; ++c) {
+    p.c[c] = sa;
+    p.c[c].cls = c;
+    p.c[c].idle_ns = 0;
+  }
+  warp_serve_kernel<EL, X3><<<unsigned(grid), kServeThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -120,6 +126,11 @@ cudaError_t dispatch(int UT, int el, bool x3, F f) {
     if (el == EL_BF16)
       return x3 ? f.template run<16, EL_BF16, true>() : f.template run<16, EL_BF16, false>();
     return x3 ? f.template run<16, EL_F16, true>() : f.template run<16, EL_F16, false>();
+  }
+  if (UT == 32) {
+    if (el == EL_BF16)
+      return x3 ? f.template run<32, EL_BF16, true>() : f.template run<32, EL_BF16, false>();
+    return x3 ? f.template run<32, EL_F16, true>() : f.template run<32, EL_F16, false>();
   }
   return cudaErrorInvalidValue;
 }
@@ -143,15 +154,6 @@ struct BatchF {
   int* g;
   template <int T, int E, bool X> cudaError_t run() { return batch<T, E, X>(op, b, mg, s, l, g); }
 };
-struct ServeF {
-  int op;
-  const ServeArgs& sa;
-  int grid;
-  cudaStream_t s;
-  bool l;
-  int* r;
-  template <int T, int E, bool X> cudaError_t run() { return serve<T, E, X>(op, sa, grid, s, l, r); }
-};
 
 }  // namespace
 
@@ -168,9 +170,13 @@ cudaError_t launch_batch_warp(int op, int UT, int el, bool x3, const BatchArgs& 
   return dispatch(UT < 8 ? 8 : UT, el, x3, BatchF{op, b, max_grid, s, launch, grid_out});
 }
 
-cudaError_t launch_serve_warp(int op, int UT, int el, bool x3, const ServeArgs& sa, int grid,
-                              cudaStream_t s, bool launch, int* resident_out) {
-  return dispatch(UT < 8 ? 8 : UT, el, x3, ServeF{op, sa, grid, s, launch, resident_out});
+cudaError_t launch_serve_warp(int el, bool x3, const ServeArgs& sa, int grid, cudaStream_t s,
+                              bool launch, int* resident_out) {
+  if (el == EL_BF16)
+    return x3 ? serve<EL_BF16, true>(sa, grid, s, launch, resident_out)
+              : serve<EL_BF16, false>(sa, grid, s, launch, resident_out);
+  return x3 ? serve<EL_F16, true>(sa, grid, s, launch, resident_out)
+            : serve<EL_F16, false>(sa, grid, s, launch, resident_out);
 }
 
 }  // namespace cgm

@@ -157,7 +157,8 @@ int main(int argc, char** argv) {
   std::vector<Flight> flight;
   std::vector<int> free_regions;
   for (int k = capacity - 1; k >= 0; --k) free_regions.push_back(k);
-  std::vector<double> lat_ms;
+  std::vector<double> lat_ms, svc_ms;  // latency from arrival; device service time (served)
+  int64_t loops = 0, submit_ns = 0, poll_ns = 0;
   std::vector<double> cls_lat[6];  // (operation, padded users 8 / 16 / 32)
   auto cls_of = [](const cg_desc& d) {
     return d.op * 3 + (d.U <= 8 ? 0 : d.U <= 16 ? 1 : 2);
@@ -188,6 +189,8 @@ int main(int argc, char** argv) {
 
   while ((next < reqs.size() || !flight.empty()) && now_ns() < deadline) {
     const int64_t now = now_ns() - t0;
+    ++loops;
+    const int64_t ts0 = now_ns();
     // submit every request that is due, while a region is free
     while (next < reqs.size() && reqs[next].arrival_ns <= now && !free_regions.empty()) {
       Req& r = reqs[next];
@@ -228,6 +231,8 @@ int main(int argc, char** argv) {
       max_inflight = std::max(max_inflight, flight.size());
       ++next;
     }
+    const int64_t ts1 = now_ns();
+    submit_ns += ts1 - ts0;
     // completions
     for (size_t k = 0; k < flight.size();) {
       const Flight f = flight[k];
@@ -240,6 +245,7 @@ int main(int argc, char** argv) {
           return 1;
         }
         done = dn != 0;
+        if (done) svc_ms.push_back(double(s.device_done_ns - s.device_first_ns) * 1e-6);
       } else {
         done = cudaEventQuery(evs[size_t(f.region)]) == cudaSuccess;
       }
@@ -256,6 +262,7 @@ int main(int argc, char** argv) {
         ++k;
       }
     }
+    poll_ns += now_ns() - ts1;
     if (served && next < reqs.size() && reqs[next].arrival_ns > now_ns() - t0 + 20000)
       std::this_thread::sleep_for(std::chrono::microseconds(5));
   }
@@ -277,10 +284,13 @@ int main(int argc, char** argv) {
   printf("{\"mode\": \"%s\", \"requests\": %zu, \"completed\": %zu, \"offered_rps\": %.1f, "
          "\"achieved_rps\": %.1f, \"solves_per_s\": %.1f, \"lat_p50_ms\": %.4f, "
          "\"lat_p99_ms\": %.4f, \"lat_mean_ms\": %.4f, \"max_inflight\": %zu, \"eagain\": %lld, "
-         "\"precision\": %d, \"per_class_count_p50_p99_ms\": %s}\n",
+         "\"precision\": %d, \"per_class_count_p50_p99_ms\": %s, "
+         "\"device_service_p50_p99_ms\": [%.4f, %.4f], \"host_loops\": %lld, "
+         "\"host_submit_s\": %.3f, \"host_poll_s\": %.3f}\n",
          mode.c_str(), reqs.size(), lat_ms.size(), reqs.size() / seconds,
          lat_ms.size() / std::max(elapsed, 1e-9), solves_done / std::max(elapsed, 1e-9),
          pct(lat_ms, 0.5), pct(lat_ms, 0.99), mean, max_inflight, (long long)eagain,
-         served ? precision : 0, per_class.c_str());
+         served ? precision : 0, per_class.c_str(), pct(svc_ms, 0.5), pct(svc_ms, 0.99),
+         (long long)loops, submit_ns * 1e-9, poll_ns * 1e-9);
   return lat_ms.size() == reqs.size() ? 0 : 2;
 }

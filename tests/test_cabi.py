@@ -108,7 +108,8 @@ def test_plan_rejects_invalid_descriptors_on_the_host(lib):
 
 
 def test_serve_rejects_invalid_configuration_on_the_host(lib):
-    for bad in (dict(capacity=0), dict(precision=0), dict(precision=7), dict(hbm_budget_bytes=0),
+    for bad in (dict(capacity=0), dict(capacity=(1 << 14) + 1), dict(precision=0),
+                dict(precision=7), dict(hbm_budget_bytes=0),
                 dict(max_B=0), dict(max_B=257), dict(max_R=17), dict(ctas_per_class=-1),
                 dict(idle_timeout_ms=0), dict(idle_timeout_ms=120000)):
         rc, srv = cabi.cg_serve_create(**bad)
