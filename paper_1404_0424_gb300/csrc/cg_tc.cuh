@@ -292,338 +292,6 @@ __device__ __forceinline__ PreItem pre_item(const BatchArgs& b, int64_t w) {
   return it;
 }
 
-// ---------------------------------------------------------------------------
-// Serving: requests published by the host, claimed instance by instance
-// ---------------------------------------------------------------------------
-
-// Serving protocol. The host publishes a request without any CUDA call:
-// it writes the request's descriptor into its slot and the class ring entry
-// (slot, instance count, ticket) into mapped host memory, then, after a
-// release fence, the new class tail. The first work unit to need the
-// request reads the tail with an acquire load, then the entry and the
-// descriptor, and copies both into device memory (ServeMirror); all other
-// work on the request reads that copy, so the link to host memory carries
-// a few words per request rather than per instance. A request's progress
-// lives in device memory, in two words of its class-ring position tagged
-// with the low 32 bits of its ticket: the first unit to see an older tag
-// starts the count afresh (compare-and-swap), so the host never resets
-// device memory; every later unit counts with a plain atomicAdd, so claims
-// do not serialise behind a compare-and-swap loop when hundreds of warps
-// take instances of one request. A ring position is given to a new request
-// only after 4 x capacity later requests of its class have been published
-// (and its own request has completed), so the tag a unit has just read is
-// still the one its atomicAdd lands on. Tickets grow by one per request, so
-// tags compare by the sign of their 32-bit difference.
-
-// Descriptor of the request in a slot (mapped host memory, host-written).
-struct ServeDesc {
-  cg_desc d;
-  unsigned long long ticket;
-};
-
-// Progress of the request at a class-ring position (device memory).
-//   claim: tag << 32 | next instance to hand out
-//   done:  tag << 32 | instances finished << 8 | OR of their status words
-struct ServeCount {
-  unsigned long long claim;
-  unsigned long long done;
-};
-
-// A published request in a class ring (mapped host memory).
-struct ServeEntry {
-  unsigned long long slot_ninst;  // slot << 32 | instance count
-  unsigned long long ticket;
-};
-
-// Completion record in mapped host memory, written by the device.
-struct ServeCompletion {
-  unsigned long long seq;  // ticket + 1 once the request is complete
-  unsigned long long t_first_ns, t_done_ns;  // device global timer
-  int status;
-  int pad;
-};
-
-constexpr int kServeTotal = 7;  // class_tail index of the total over all classes
-
-// Control block in mapped host memory: the stop flag and the class tails
-// (host-written), and per serving kernel the number of running work units
-// (CTAs or warps) and the launch generation whose last unit has exited
-// (device-written), which let the host see whether a kernel is alive
-// without a CUDA call.
-
-struct ServeCtrl {
-  unsigned long long class_tail[8];  // requests published per class; [7]: all classes
-  int stop;
-  int pad;
-  int live[8];
-  unsigned long long exited_gen[8];
-};
-
-// Threads of a serving CTA of the warp-per-instance kernels (8 warps: one
-// such CTA fills an SM's share of the serving grid).
-constexpr int kServeThreads = 256;
-
-// Device copy of a published request, one per class-ring position: its
-// descriptor and ring entry, valid when seq is the class sequence number of
-// the request plus one. The first unit that needs the request and finds the
-// copy missing reads the mapped host memory once and writes it (several
-// units may race to write the same values); every other claim, descriptor
-// read and completion of the request then stays in device memory.
-struct __align__(16) ServeMirror {
-  cg_desc d;
-  unsigned long long slot_ninst;
-  unsigned long long ticket;
-  unsigned long long seq;
-  unsigned long long pad;
-};
-
-struct ServeArgs {
-  ServeCount* counts;           // device, one per class-ring position
-  ServeMirror* mirror;          // device, one per class-ring position
-  const ServeDesc* descs;       // mapped host, one per slot
-  const ServeEntry* class_ring; // mapped host: [class][cap] published entries
-  ServeCtrl* ctrl;              // mapped host
-  ServeCompletion* comp;        // mapped host, one per slot
-  unsigned long long* class_head;  // device: first request of the class with work left
-  int cls, cap;                 // cap: ring positions per class
-  int PB, PR, PEX;
-  unsigned long long idle_ns;   // exit after this long without work
-  unsigned long long gen;       // launch generation of this kernel
-};
-
-template <class T>
-__device__ __forceinline__ T volatile_load(const T* p) {
-  return *const_cast<const volatile T*>(p);
-}
-
-__device__ __forceinline__ unsigned long long load_acquire_sys(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// True when tag a belongs to an earlier request than tag b.
-__device__ __forceinline__ bool tag_older(unsigned long long a, unsigned long long b) {
-  return int32_t(uint32_t(a) - uint32_t(b)) < 0;
-}
-
-// A work unit (CTA or warp, one thread calls) starts or ends serving its
-// class. The unit that brings the count to zero records the generation.
-__device__ __forceinline__ void serve_unit_enter(const ServeArgs& s) {
-  atomicAdd_system(&s.ctrl->live[s.cls], 1);
-}
-__device__ __forceinline__ void serve_unit_exit(const ServeArgs& s) {
-  __threadfence_system();
-  if (atomicSub_system(&s.ctrl->live[s.cls], 1) == 1)
-    atomicMax_system(&s.ctrl->exited_gen[s.cls], s.gen);
-}
-
-// A serving work unit: slot << 45 | class-ring position << 24 | instance
-// (slots < 2^18, positions < 2^21, instances < 2^24).
-__device__ __forceinline__ int64_t serve_unit(int sl, unsigned pos, unsigned long long inst) {
-  return (int64_t(sl) << 45) | (int64_t(pos) << 24) | int64_t(inst);
-}
-__device__ __forceinline__ int unit_slot(int64_t w) { return int(w >> 45); }
-__device__ __forceinline__ unsigned unit_pos(int64_t w) { return unsigned(w >> 24) & 0x1fffffu; }
-__device__ __forceinline__ int unit_inst(int64_t w) { return int(w & 0xffffff); }
-
-__device__ __forceinline__ unsigned serve_pos(const ServeArgs& s, unsigned long long head) {
-  return unsigned(s.cls) * unsigned(s.cap) + unsigned(head % unsigned(s.cap));
-}
-
-// 8-byte word copies (volatile: they bypass L1, whose lines could be stale
-// for a position or slot reused since).
-template <class T>
-__device__ __forceinline__ void copy_words_volatile(T* dst, const T* src) {
-  static_assert(sizeof(T) % 8 == 0, "copied in 8-byte words");
-  const unsigned long long* a = reinterpret_cast<const unsigned long long*>(src);
-  unsigned long long* b = reinterpret_cast<unsigned long long*>(dst);
-#pragma unroll
-  for (int k = 0; k < int(sizeof(T) / 8); ++k)
-    *const_cast<volatile unsigned long long*>(b + k) = volatile_load(a + k);
-}
-
-// The device copy of the request at sequence number `head` of the class, once
-// that request is known to be published (head < class tail, read with
-// acquire). Fills it from mapped host memory if it is missing.
-__device__ __forceinline__ const ServeMirror* serve_fill_mirror(const ServeArgs& s,
-                                                                unsigned long long head) {
-  const unsigned pos = serve_pos(s, head);
-  ServeMirror* m = s.mirror + pos;
-  if (volatile_load(&m->seq) == head + 1) {
-    __threadfence();  // the copy's fields after its valid mark
-    return m;
-  }
-  const ServeEntry* ep = s.class_ring + pos;
-  const unsigned long long sn = volatile_load(&ep->slot_ninst);
-  const unsigned long long t = volatile_load(&ep->ticket);
-  copy_words_volatile(&m->d, &s.descs[int(sn >> 32)].d);
-  *const_cast<volatile unsigned long long*>(&m->slot_ninst) = sn;
-  *const_cast<volatile unsigned long long*>(&m->ticket) = t;
-  __threadfence();  // the fields before the valid mark
-  *const_cast<volatile unsigned long long*>(&m->seq) = head + 1;
-  return m;
-}
-
-// The device copy of the request at sequence number `head` if it is already
-// valid (then the request is published and no host memory is read), else
-// nullptr.
-__device__ __forceinline__ const ServeMirror* serve_valid_mirror(const ServeArgs& s,
-                                                                 unsigned long long head) {
-  const ServeMirror* m = s.mirror + serve_pos(s, head);
-  if (volatile_load(&m->seq) != head + 1) return nullptr;
-  __threadfence();
-  return m;
-}
-
-// One claim attempt on the request at the class head (its device copy m).
-// Returns the claimed work unit, or -1 when that request has nothing left to
-// hand out (the head is then advanced past it).
-__device__ __forceinline__ int64_t serve_claim_at(const ServeArgs& s, unsigned long long head,
-                                                  const ServeMirror* m) {
-  const unsigned pos = serve_pos(s, head);
-  const unsigned long long sn = volatile_load(&m->slot_ninst);
-  const unsigned long long ticket = volatile_load(&m->ticket);
-  const int sl = int(sn >> 32);
-  const unsigned long long n = sn & 0xffffffffull;
-  const unsigned long long tag = ticket & 0xffffffffull;
-  unsigned long long* cw = &s.counts[pos].claim;
-  unsigned long long w = volatile_load(cw);
-  while (true) {
-    const unsigned long long wt = w >> 32;
-    if (wt == tag) {
-      if ((w & 0xffffffffull) >= n) break;  // fully handed out
-      const unsigned long long old = atomicAdd(cw, 1ull);
-      const unsigned long long inst = old & 0xffffffffull;
-      if ((old >> 32) != tag || inst >= n) break;
-      return serve_unit(sl, pos, inst);
-    }
-    if (!tag_older(wt, tag)) break;  // a later request holds the position: this one is done
-    // first claim of this request: the word still holds an earlier one
-    const unsigned long long prev = atomicCAS(cw, w, (tag << 32) | 1ull);
-    if (prev == w) {
-      s.comp[sl].t_first_ns = global_timer_ns();
-      return serve_unit(sl, pos, 0);
-    }
-    w = prev;
-  }
-  atomicCAS(&s.class_head[s.cls], head, head + 1ull);  // request fully handed out
-  return -1;
-}
-
-// One claim of the request at the head, if there is one: through its valid
-// device copy, else after reading the class tail (acquire) and filling the
-// copy. -1: that request is fully handed out; -2: nothing is published.
-__device__ __forceinline__ int64_t serve_claim_head(const ServeArgs& s) {
-  const unsigned long long head = volatile_load(&s.class_head[s.cls]);
-  const ServeMirror* m = serve_valid_mirror(s, head);
-  if (m == nullptr) {
-    if (head >= load_acquire_sys(&s.ctrl->class_tail[s.cls])) return -2;
-    m = serve_fill_mirror(s, head);
-  }
-  return serve_claim_at(s, head, m);
-}
-
-// One thread finds an unclaimed instance of the oldest request of its class
-// and returns it. Waits are bounded: -1 on the stop flag or after idle_ns of
-// global time without work.
-__device__ __forceinline__ int64_t serve_claim_wait(const ServeArgs& s) {
-  const uint64_t t0 = global_timer_ns();
-  while (true) {
-    const int64_t w = serve_claim_head(s);
-    if (w >= 0) return w;
-    if (w == -1) continue;  // the head moved on: try the next request
-    if (volatile_load(&s.ctrl->stop)) return -1;
-    if (global_timer_ns() - t0 > s.idle_ns) return -1;
-    __nanosleep(256);
-  }
-}
-
-// Thread 0 claims for its CTA (serve_claim_wait) into shared memory.
-__device__ __forceinline__ void claim_next(const ServeArgs& s, int64_t* slot) {
-  if (threadIdx.x != 0) return;
-  *slot = serve_claim_wait(s);
-}
-
-// Non-blocking claim by one thread: -2 when no work is available yet (try
-// again later; the stop flag is seen by the waiting claim that follows).
-__device__ __forceinline__ int64_t serve_claim_try(const ServeArgs& s) {
-  while (true) {
-    const int64_t w = serve_claim_head(s);
-    if (w != -1) return w;
-  }
-}
-
-// Thread 0 of a CTA, non-blocking (serve_claim_try) into shared memory.
-__device__ __forceinline__ void claim_try(const ServeArgs& s, int64_t* slot) {
-  if (threadIdx.x != 0) return;
-  *slot = serve_claim_try(s);
-}
-
-// The descriptor of a work unit's request, from its device copy.
-__device__ __forceinline__ cg_desc serve_desc(const ServeArgs& s, int64_t w) {
-  cg_desc d;
-  copy_words_volatile(&d, &s.mirror[unit_pos(w)].d);
-  return d;
-}
-
-// Thread 0, after an instance's outputs and status are stored: counts it and,
-// for the request's last instance, publishes the completion to the host.
-__device__ __forceinline__ void serve_done(const ServeArgs& s, int64_t w, int status) {
-  const int sl = unit_slot(w);
-  const unsigned pos = unit_pos(w);
-  const ServeMirror* m = s.mirror + pos;
-  const unsigned long long n = volatile_load(&m->slot_ninst) & 0xffffffffull;
-  const unsigned long long ticket = volatile_load(&m->ticket);
-  const unsigned long long tag = ticket & 0xffffffffull;
-  const unsigned long long st = (unsigned long long)(status & 0xff);
-  __threadfence_system();  // the instance's outputs before its count
-  unsigned long long* dw = &s.counts[pos].done;
-  unsigned long long v = volatile_load(dw), now = 0;
-  while (true) {
-    if ((v >> 32) == tag) {
-      // the status bits first, so that the last count sees every instance's
-      if (st) atomicOr(dw, st);
-      now = (atomicAdd(dw, 1ull << 8) + (1ull << 8)) | st;
-      break;
-    }
-    // first finished instance of this request: start the count
-    const unsigned long long next = (tag << 32) | (1ull << 8) | st;
-    const unsigned long long prev = atomicCAS(dw, v, next);
-    if (prev == v) {
-      now = next;
-      break;
-    }
-    v = prev;
-  }
-  if (((now >> 8) & 0xffffffull) == n) {
-    __threadfence_system();
-    ServeCompletion* c = s.comp + sl;
-    c->status = int(now & 0xffull);
-    c->t_done_ns = global_timer_ns();
-    __threadfence_system();
-    *const_cast<volatile unsigned long long*>(&c->seq) = ticket + 1;
-  }
-}
-
-__device__ __forceinline__ DetItem det_item(const ServeArgs& s, int64_t w) {
-  const cg_desc d = serve_desc(s, w);
-  const int2 wu = make_int2(0, unit_inst(w));
-  BatchArgs b{};
-  b.desc = &d;
-  b.work = &wu;
-  return det_item(b, 0);
-}
-
-__device__ __forceinline__ PreItem pre_item(const ServeArgs& s, int64_t w) {
-  const cg_desc d = serve_desc(s, w);
-  const int2 wu = make_int2(0, unit_inst(w));
-  BatchArgs b{};
-  b.desc = &d;
-  b.work = &wu;
-  return pre_item(b, 0);
-}
-
 // Claims the next work unit of a batch: thread 0 bumps the counter and
 // publishes the index in shared memory; readers wait for the next barrier.
 __device__ __forceinline__ void claim_next(const BatchArgs& b, int64_t* slot) {
@@ -1197,24 +865,20 @@ struct TcCg {
 
 // Work source traits: DetectArgs / PrecodeArgs describe one shape for the
 // whole launch (instances taken by grid stride); BatchArgs hands out
-// (problem, instance) units of uneven shapes from a device counter.
+// (problem, instance) units of uneven shapes from a device counter (and the
+// serving sources of cg_serve.cuh hand out units of published requests).
 template <class S> struct SrcTraits;
 template <> struct SrcTraits<DetectArgs> { static constexpr bool kDyn = false; };
 template <> struct SrcTraits<PrecodeArgs> { static constexpr bool kDyn = false; };
 template <> struct SrcTraits<BatchArgs> { static constexpr bool kDyn = true; };
-template <> struct SrcTraits<ServeArgs> { static constexpr bool kDyn = true; };
 
-// Per-instance completion hook (serving only).
+// Per-instance completion hook (a no-op except for serving sources).
 template <class S>
 __device__ __forceinline__ void src_done(const S&, int64_t, int) {}
-__device__ __forceinline__ void src_done(const ServeArgs& s, int64_t w, int status) {
-  serve_done(s, w, status);
-}
 
 __device__ __forceinline__ int64_t src_count(const DetectArgs& a) { return a.n_inst; }
 __device__ __forceinline__ int64_t src_count(const PrecodeArgs& a) { return a.n_inst; }
 __device__ __forceinline__ int64_t src_count(const BatchArgs& b) { return b.n_work; }
-__device__ __forceinline__ int64_t src_count(const ServeArgs&) { return 0; }
 
 template <int UT, int EL, bool X3, bool FULL, class Src>
 __device__ __forceinline__ void detect_tc_body(const Src& src, int PB, int PU, int PR,
@@ -1674,24 +1338,6 @@ template <int UT, int EL, bool X3, bool FULL>
 __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
     precode_tc_batch_kernel(const BatchArgs b) {
   precode_tc_body<UT, EL, X3, FULL>(b, b.PB, UT, b.PR);
-}
-
-// Serving kernels: one per (operation, padded user count); every CTA claims
-// instances of the oldest request of its class until stopped or idle.
-template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
-    detect_tc_serve_kernel(const ServeArgs s) {
-  if (threadIdx.x == 0) serve_unit_enter(s);
-  detect_tc_body<UT, EL, X3, false>(s, s.PB, UT, s.PR, s.PEX);
-  if (threadIdx.x == 0) serve_unit_exit(s);
-}
-
-template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
-    precode_tc_serve_kernel(const ServeArgs s) {
-  if (threadIdx.x == 0) serve_unit_enter(s);
-  precode_tc_body<UT, EL, X3, false>(s, s.PB, UT, s.PR);
-  if (threadIdx.x == 0) serve_unit_exit(s);
 }
 
 }  // namespace cgm

@@ -583,11 +583,6 @@ __device__ __forceinline__ int64_t warp_claim(const BatchArgs& b) {
   return __shfl_sync(0xffffffffu, w, 0);
 }
 
-__device__ __forceinline__ int64_t warp_claim(const ServeArgs& s) {
-  int64_t w = -1;
-  if ((threadIdx.x & 31) == 0) w = serve_claim_wait(s);
-  return __shfl_sync(0xffffffffu, w, 0);
-}
 
 template <class S>
 __device__ __forceinline__ int64_t warp_first(const S& s, int64_t gw) {
@@ -834,11 +829,6 @@ __device__ __forceinline__ bool detect_vec(const DetItem& it) {
 
 // Claim without waiting: -2 when a serving queue has nothing yet.
 __device__ __forceinline__ int64_t warp_try(const BatchArgs& b) { return warp_claim(b); }
-__device__ __forceinline__ int64_t warp_try(const ServeArgs& s) {
-  int64_t w = -1;
-  if ((threadIdx.x & 31) == 0) w = serve_claim_try(s);
-  return __shfl_sync(0xffffffffu, w, 0);
-}
 
 // Next unit of a warp while it still works on `cur` (-1: none, -2: ask again later).
 template <class S>
@@ -1119,116 +1109,6 @@ template <int UT, int EL, bool X3>
 __global__ void __launch_bounds__(WarpCfg<UT>::NTHR, WarpCfg<UT>::MINB)
     precode_warp_batch_kernel(const BatchArgs b) {
   precode_warp_body<UT, EL, X3>(b, warp_slice<WarpCfg<UT>::FRAG_BYTES>());
-}
-
-// ---------------------------------------------------------------------------
-// Serving: one kernel for the six (operation, padded users) classes of the
-// approximate tracker
-// ---------------------------------------------------------------------------
-
-// Classes 0-2 detect with 8, 16, 32 padded users, 3-5 precode.
-constexpr int kWarpClasses = 6;
-// Every warp owns a slice large enough for any class, since the warps of one
-// CTA may serve different classes at the same time.
-constexpr uint32_t kServeSlice = WarpCfg<32>::WARP_BYTES;
-static_assert(WarpCfg<8>::WARP_BYTES <= kServeSlice && WarpCfg<16>::WARP_BYTES <= kServeSlice &&
-                  WarpCfg<32>::FRAG_BYTES <= kServeSlice,
-              "serving slice must hold every class");
-
-// Kernel parameters: the kernel's own ServeArgs (cls = its liveness counter,
-// idle_ns = its idle limit) and one copy per class with cls = the class and
-// idle_ns = 0, so that a class body returns once its class has no work. The
-// copies live in the parameter space, which the bodies read in place.
-struct ServeWarpArgs {
-  ServeArgs k;
-  ServeArgs c[kWarpClasses];
-};
-
-// One class body as a called function, so that each class keeps the
-// register allocation it has in its own kernel.
-template <int UT, int EL, bool X3>
-__device__ __noinline__ void serve_detect(const ServeArgs& s, unsigned char* mine) {
-  detect_warp_body<UT, EL, X3>(s, mine);
-}
-template <int UT, int EL, bool X3>
-__device__ __noinline__ void serve_precode(const ServeArgs& s, unsigned char* mine) {
-  precode_warp_body<UT, EL, X3>(s, mine);
-}
-
-template <int EL, bool X3>
-__device__ __forceinline__ void serve_class(int c, const ServeWarpArgs& p, unsigned char* mine) {
-  switch (c) {
-    case 0: serve_detect<8, EL, X3>(p.c[0], mine); break;
-    case 1: serve_detect<16, EL, X3>(p.c[1], mine); break;
-    case 2: serve_detect<32, EL, X3>(p.c[2], mine); break;
-    case 3: serve_precode<8, EL, X3>(p.c[3], mine); break;
-    case 4: serve_precode<16, EL, X3>(p.c[4], mine); break;
-    default: serve_precode<32, EL, X3>(p.c[5], mine); break;
-  }
-}
-
-// Lane 0: the first class, starting at `home`, that has a published request
-// at its head (seen from the request's device copy when there is one, else
-// from the class tail), or -1.
-__device__ __forceinline__ int serve_pick(const ServeArgs& s, int home) {
-  for (int j = 0; j < kWarpClasses; ++j) {
-    const int c = home + j < kWarpClasses ? home + j : home + j - kWarpClasses;
-    const unsigned long long head = volatile_load(&s.class_head[c]);
-    const ServeMirror* m = s.mirror + unsigned(c) * unsigned(s.cap) + unsigned(head % unsigned(s.cap));
-    if (volatile_load(&m->seq) == head + 1) return c;
-    if (head < load_acquire_sys(&s.ctrl->class_tail[c])) return c;
-  }
-  return -1;
-}
-
-// Each warp serves its home class (warps are spread evenly over the classes)
-// while that class has work, and otherwise the next class in turn that has
-// some, so a request can use every warp of the grid when the others are
-// idle. A class body returns as soon as its class has nothing left to hand
-// out. Idle warps read the published-request total (one word of mapped host
-// memory) and look at the class tails only when it has moved; they exit
-// after idle_ns without work or on the stop flag. s.cls is the liveness
-// counter of this kernel.
-template <int EL, bool X3>
-__global__ void __launch_bounds__(kServeThreads, 1)
-    warp_serve_kernel(const __grid_constant__ ServeWarpArgs p) {
-  const ServeArgs& s = p.k;
-  const int lane = threadIdx.x & 31;
-  unsigned char* mine = warp_slice<kServeSlice>();
-  if (lane == 0) serve_unit_enter(s);
-  const int home = int((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kWarpClasses);
-  unsigned long long t_idle = global_timer_ns(), seen = ~0ull;
-  unsigned sleep_ns = 128;
-  while (true) {
-    int pick = -1;
-    if (lane == 0) {
-      if (volatile_load(&s.ctrl->stop)) {
-        pick = -2;
-      } else {
-        const unsigned long long total = load_acquire_sys(&s.ctrl->class_tail[kServeTotal]);
-        if (total != seen) {
-          pick = serve_pick(s, home);
-          if (pick < 0) seen = total;  // nothing new until the total moves
-        }
-        if (pick == -1) {
-          if (global_timer_ns() - t_idle > s.idle_ns) {
-            pick = -2;
-          } else {
-            __nanosleep(sleep_ns);
-            sleep_ns = sleep_ns < 2048 ? 2 * sleep_ns : 2048;
-          }
-        }
-      }
-    }
-    pick = __shfl_sync(0xffffffffu, pick, 0);
-    if (pick == -2) break;
-    if (pick < 0) continue;
-    serve_class<EL, X3>(pick, p, mine);
-    t_idle = global_timer_ns();
-    sleep_ns = 128;
-    seen = ~0ull;
-  }
-  if (lane == 0) serve_unit_exit(s);
 }
 
 }  // namespace cgm

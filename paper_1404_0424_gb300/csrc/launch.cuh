@@ -52,21 +52,20 @@ cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const Ba
                             int max_grid, cudaStream_t s, bool launch, uint32_t* smem_out,
                             int* grid_out);
 
-// CTA serving kernels (tc.cu), used for exact-tracker detection: one
-// persistent kernel per (operation, UT). With launch = false only the
-// shared-memory size and resident CTAs are computed.
-cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
-                            cudaStream_t st, bool launch, uint32_t* smem_out, int* resident_out);
-
 // Warp-per-instance kernels (warp.cu): padded users 8, 16 or 32, approximate
 // tracker only. Batch and serve forms as above (grid in CTAs of 4 warps).
 cudaError_t launch_detect_warp(int UT, int el, bool x3, const DetectArgs& a, cudaStream_t s);
 cudaError_t launch_precode_warp(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s);
 cudaError_t launch_batch_warp(int op, int UT, int el, bool x3, const BatchArgs& b, int max_grid,
                               cudaStream_t s, bool launch, int* grid_out);
-// The serving kernel of the six approximate-tracker classes (warp_serve_kernel).
+// Serving kernels (serve_kernels.cu): the warp kernel of the six
+// approximate-tracker classes and the CTA kernels of exact-tracker
+// detection. With launch = false only the resident CTAs are computed.
+struct ServeArgs;
 cudaError_t launch_serve_warp(int el, bool x3, const ServeArgs& sa, int grid, cudaStream_t s,
                               bool launch, int* resident_out);
+cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
+                            cudaStream_t st, bool launch, int* resident_out);
 
 // Implicit-product FP32 kernels (implicit.cu): e = H^H (H p) + sigma p.
 cudaError_t launch_detect_implicit(int UT, const DetectArgs& a, cudaStream_t s);

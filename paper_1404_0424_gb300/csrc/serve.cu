@@ -18,6 +18,7 @@
 
 #include "cgmimo.h"
 #include "host_checks.h"
+#include "cg_serve.cuh"
 #include "launch.cuh"
 
 using namespace cgm;
@@ -124,6 +125,7 @@ ServeArgs args_for(const cg_server* s, int k) {
   a.PB = s->cfg.max_B;
   a.PR = s->cfg.max_R;
   a.PEX = k == 1 ? 1 : 0;
+  a.poll_host = 1;
   a.idle_ns = (unsigned long long)s->cfg.idle_timeout_ms * 1000000ull;
   a.gen = s->launched_gen[k];
   return a;
@@ -133,7 +135,7 @@ ServeArgs args_for(const cg_server* s, int k) {
 cudaError_t launch_kernel(const cg_server* s, int k, bool launch, int* resident) {
   const ServeArgs a = args_for(s, k);
   if (k == 0) return launch_serve_warp(s->el, s->x3, a, s->grid[0], s->ks[0], launch, resident);
-  return launch_serve_tc(CG_OP_DETECT, 32, s->el, s->x3, a, s->grid[1], s->ks[1], launch, nullptr,
+  return launch_serve_tc(CG_OP_DETECT, 32, s->el, s->x3, a, s->grid[1], s->ks[1], launch,
                          resident);
 }
 
@@ -221,7 +223,7 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
   const size_t positions = size_t(kClasses) * size_t(s->ring);
   const size_t mirror_off = (sizeof(ServeCount) * positions + 255) & ~size_t(255);
   const size_t head_off = mirror_off + sizeof(ServeMirror) * positions;
-  const size_t dbytes = head_off + sizeof(unsigned long long) * 8;
+  const size_t dbytes = head_off + sizeof(unsigned long long) * kServeHeadWords;
   const size_t comp_off = (sizeof(ServeCtrl) + 255) & ~size_t(255);
   const size_t desc_off = comp_off + sizeof(ServeCompletion) * cap;
   const size_t ring_off = desc_off + sizeof(ServeDesc) * cap;

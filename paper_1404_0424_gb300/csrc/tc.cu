@@ -212,59 +212,3 @@ cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const Ba
 }
 
 }  // namespace cgm
-
-// ---------------------------------------------------------------------------
-// Serving kernels
-// ---------------------------------------------------------------------------
-
-namespace cgm {
-
-namespace {
-
-template <int UT, int EL, bool X3>
-cudaError_t serve_t(int op, const ServeArgs& s, int grid, cudaStream_t st, bool launch,
-                    uint32_t* smem_out, int* resident_out) {
-  constexpr int NTHR = TcCfg<UT>::NTHR;
-  DeviceInfo di;
-  if (device_info(&di) != 0) return cudaErrorUnknown;
-  // padded to one CTA per SM like every serving CTA
-  const uint32_t smem = serve_smem(di, op == 0 ? tc_detect_plan<UT>(s.PB, UT, s.PR, s.PEX).total
-                                               : tc_precode_plan<UT>(s.PB, UT, s.PR).total);
-  int slots = 0;
-  const uint64_t id = (op == 0 ? 0x10000 : 0x20000) | (UT << 3) | (EL << 2) | (X3 ? 2 : 0);
-  cudaError_t err = op == 0 ? prepare(detect_tc_serve_kernel<UT, EL, X3>, id, NTHR, smem, &slots)
-                            : prepare(precode_tc_serve_kernel<UT, EL, X3>, id, NTHR, smem, &slots);
-  if (err != cudaSuccess) return err;
-  if (smem_out) *smem_out = smem;
-  if (resident_out) *resident_out = slots;
-  if (!launch) return cudaSuccess;
-  if (op == 0)
-    detect_tc_serve_kernel<UT, EL, X3><<<unsigned(grid), NTHR, smem, st>>>(s);
-  else
-    precode_tc_serve_kernel<UT, EL, X3><<<unsigned(grid), NTHR, smem, st>>>(s);
-  return cudaGetLastError();
-}
-
-template <int UT>
-cudaError_t serve_ut(int op, int el, bool x3, const ServeArgs& s, int grid, cudaStream_t st,
-                     bool l, uint32_t* sm, int* res) {
-  if (el == EL_BF16)
-    return x3 ? serve_t<UT, EL_BF16, true>(op, s, grid, st, l, sm, res)
-              : serve_t<UT, EL_BF16, false>(op, s, grid, st, l, sm, res);
-  return x3 ? serve_t<UT, EL_F16, true>(op, s, grid, st, l, sm, res)
-            : serve_t<UT, EL_F16, false>(op, s, grid, st, l, sm, res);
-}
-
-}  // namespace
-
-cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
-                            cudaStream_t st, bool launch, uint32_t* smem_out, int* resident_out) {
-  switch (UT) {
-    case 8: return serve_ut<8>(op, el, x3, s, grid, st, launch, smem_out, resident_out);
-    case 16: return serve_ut<16>(op, el, x3, s, grid, st, launch, smem_out, resident_out);
-    case 32: return serve_ut<32>(op, el, x3, s, grid, st, launch, smem_out, resident_out);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-}  // namespace cgm

@@ -92,29 +92,6 @@ cudaError_t batch(int op, const BatchArgs& b, int max_grid, cudaStream_t s, bool
   return cudaGetLastError();
 }
 
-template <int EL, bool X3>
-cudaError_t serve(const ServeArgs& sa, int grid, cudaStream_t s, bool launch, int* resident_out) {
-  DeviceInfo di;
-  if (device_info(&di) != 0) return cudaErrorUnknown;
-  // a slice for the largest class per warp, padded to one CTA per SM
-  const uint32_t smem = serve_smem(di, uint32_t(kServeThreads / 32) * kServeSlice);
-  int res = 0;
-  const uint64_t id = 0x4000 | (EL << 1) | (X3 ? 1 : 0);
-  cudaError_t err = resident_ctas(warp_serve_kernel<EL, X3>, id, smem, &res, kServeThreads);
-  if (err != cudaSuccess) return err;
-  if (resident_out) *resident_out = res;
-  if (!launch) return cudaSuccess;
-  ServeWarpArgs p;
-  p.k = sa;
-  for (int c = 0; c < kWarpClasses; ++c) {
-    p.c[c] = sa;
-    p.c[c].cls = c;
-    p.c[c].idle_ns = 0;
-  }
-  warp_serve_kernel<EL, X3><<<unsigned(grid), kServeThreads, smem, s>>>(p);
-  return cudaGetLastError();
-}
-
 // Dispatch over (UT, EL, X3); F is called as F.template run<UT, EL, X3>().
 template <class F>
 cudaError_t dispatch(int UT, int el, bool x3, F f) {
@@ -168,15 +145,6 @@ cudaError_t launch_precode_warp(int UT, int el, bool x3, const PrecodeArgs& a, c
 cudaError_t launch_batch_warp(int op, int UT, int el, bool x3, const BatchArgs& b, int max_grid,
                               cudaStream_t s, bool launch, int* grid_out) {
   return dispatch(UT < 8 ? 8 : UT, el, x3, BatchF{op, b, max_grid, s, launch, grid_out});
-}
-
-cudaError_t launch_serve_warp(int el, bool x3, const ServeArgs& sa, int grid, cudaStream_t s,
-                              bool launch, int* resident_out) {
-  if (el == EL_BF16)
-    return x3 ? serve<EL_BF16, true>(sa, grid, s, launch, resident_out)
-              : serve<EL_BF16, false>(sa, grid, s, launch, resident_out);
-  return x3 ? serve<EL_F16, true>(sa, grid, s, launch, resident_out)
-            : serve<EL_F16, false>(sa, grid, s, launch, resident_out);
 }
 
 }  // namespace cgm
