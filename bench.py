@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the FP32 plain path")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 256x32 workload")
+    ap.add_argument("--no-neumann", action="store_true", help="skip the Neumann comparator")
+    ap.add_argument("--no-cgls", action="store_true", help="skip the CGLS comparator")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the K / U / A p sweep")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     return ap.parse_args()
@@ -457,6 +460,103 @@ def run_ours(args):
                  "value": round(2 * n * R / ((pd + pq) / 1e3), 1), "unit": "solves/s",
                  "detect_ms": round(pd, 4), "precode_ms": round(pq, 4)}
 
+    # the Neumann-series comparator (Sec. III-F) on the same batch, K = 3 terms
+    neumann = None
+    if not args.no_neumann and prec != 0:
+        pn = cabi.params(B, Un, QAM, K, R, N0, precision=prec)
+        for _ in range(2):
+            cabi.cg_neumann_detect(pn, n, H, Y, xhat, st, stream)
+            cabi.cg_neumann_precode(pn, n, H, T, q, qn, 0, stp, stream)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        reps = 5
+        e[0].record(stream)
+        for _ in range(reps):
+            rc = cabi.cg_neumann_detect(pn, n, H, Y, xhat, st, stream)
+        e[1].record(stream)
+        for _ in range(reps):
+            rc |= cabi.cg_neumann_precode(pn, n, H, T, q, qn, 0, stp, stream)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        if rc:
+            raise RuntimeError(cabi.cg_strerror(rc))
+        nd, nq = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+        nbytes = n * ((B * Un + R * B) * 8 + R * Un * 8 + 4)
+        neumann = {"what": f"truncated Neumann series, {K} terms (Sec. III-F): x_hat only "
+                           "(detection) and q, ||q|| (precoding), same batch and precision",
+                   "detect_ms": round(nd, 4), "precode_ms": round(nq, 4),
+                   "solves_per_s": round(2 * n * R / ((nd + nq) / 1e3), 1),
+                   "detect_gbs": round(nbytes / nd / 1e6, 1),
+                   "precode_gbs": round(precode_bytes_per_instance(B, Un, R) * n / nq / 1e6, 1)}
+
+    # the rest of the 128-antenna configuration on the same batch: K in {2, 3, 4},
+    # U = 8 (the first 8 users' columns would change the data, so U = 8 draws its
+    # own channels), and the implicit product against the explicit Gram
+    sweep = None
+    if not args.no_sweep and prec != 0:
+        def pair_ms(pp, Hh, Yy, Tt, nn, xo, mo, ro, lo, so, qo, qno, spo, reps=3):
+            for _ in range(2):
+                cabi.cg_detect(pp, nn, Hh, Yy, xo, mo, ro, lo, so, stream)
+                cabi.cg_precode(pp, nn, Hh, Tt, qo, qno, 0, spo, stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            rcs = 0
+            for _ in range(reps):
+                rcs |= cabi.cg_detect(pp, nn, Hh, Yy, xo, mo, ro, lo, so, stream)
+                rcs |= cabi.cg_precode(pp, nn, Hh, Tt, qo, qno, 0, spo, stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if rcs:
+                raise RuntimeError(cabi.cg_strerror(rcs))
+            return ev[0].elapsed_time(ev[1]) / reps
+        sweep = {"what": "detect + precode per step, ms, same batch of 38,400 instances"}
+        for kk in (2, 3, 4):
+            sweep[f"U16_K{kk}_{args.precision}"] = round(pair_ms(
+                cabi.params(B, Un, QAM, kk, R, N0, precision=prec), H, Y, T, n, xhat, mu, rho,
+                llr, st, q, qn, stp), 4)
+        sweep["U16_K3_fp32_explicit"] = round(pair_ms(
+            cabi.params(B, Un, QAM, K, R, N0, precision=0, amul_mode=1), H, Y, T, n, xhat, mu,
+            rho, llr, st, q, qn, stp), 4)
+        sweep["U16_K3_fp32_implicit"] = round(pair_ms(
+            cabi.params(B, Un, QAM, K, R, N0, precision=0, amul_mode=2), H, Y, T, n, xhat, mu,
+            rho, llr, st, q, qn, stp), 4)
+        u8 = wl.uplink_torch(B, 8, QAM, n=n, R=R, snr_db=SNR_DB, seed=3000 + rank, device=dev)
+        H8, Y8, T8 = u8["H"], u8["Y"], u8["x"].contiguous()
+        x8 = torch.empty((n, R, 8), dtype=torch.complex64, device=dev)
+        m8 = torch.empty((n, R, 8), dtype=torch.float32, device=dev)
+        r8 = torch.empty_like(m8)
+        l8 = torch.empty((n, R, 8, QAM), dtype=torch.float32, device=dev)
+        for kk in (2, 3, 4):
+            sweep[f"U8_K{kk}_{args.precision}"] = round(pair_ms(
+                cabi.params(B, 8, QAM, kk, R, u8["N0"], precision=prec), H8, Y8, T8, n, x8, m8,
+                r8, l8, st, q, qn, stp), 4)
+        del u8, H8, Y8, T8, x8, m8, r8, l8
+        sweep["solves_per_step"] = 2 * n * R
+
+    # CG least squares (Sec. III-E, no Gram, FP32 CUDA cores) on the same batch
+    cgls = None
+    if not args.no_cgls:
+        pc = cabi.params(B, Un, QAM, K, R, N0, amul_mode=3)
+        for _ in range(2):
+            cabi.cg_detect(pc, n, H, Y, xhat, mu, rho, llr, st, stream)
+            cabi.cg_precode(pc, n, H, T, q, qn, 0, stp, stream)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        reps = 3
+        e[0].record(stream)
+        for _ in range(reps):
+            rc = cabi.cg_detect(pc, n, H, Y, xhat, mu, rho, llr, st, stream)
+        e[1].record(stream)
+        for _ in range(reps):
+            rc |= cabi.cg_precode(pc, n, H, T, q, qn, 0, stp, stream)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        if rc:
+            raise RuntimeError(cabi.cg_strerror(rc))
+        cd, cq = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+        cgls = {"what": f"CG least squares, {K} iterations (Sec. III-E): no Gram, FP32 CUDA "
+                        "cores, all outputs, same batch",
+                "detect_ms": round(cd, 4), "precode_ms": round(cq, 4),
+                "solves_per_s": round(2 * n * R / ((cd + cq) / 1e3), 1)}
+
     # plain per-call latency: one 1200 x 14 slot (detect + precode) per call
     lat = []
     Hs, Ys, Ts = H[:NSC], Y[:NSC], T[:NSC]
@@ -568,6 +668,9 @@ def run_ours(args):
                            "plain_p99": (serving or {}).get("plain", {}).get("lat_p99_ms")},
             "batched": batched,
             "large_256x32": large,
+            "neumann": neumann,
+            "cgls": cgls,
+            "sweep_128": sweep,
             "serving": serving,
             "roofline": roofline,
             "plain_fp32": plain,

@@ -80,6 +80,16 @@ extern "C" {
 #define CG_AMUL_AUTO 0      /* library choice (above) */
 #define CG_AMUL_EXPLICIT 1  /* form A = H^H H + (N0/Es) I once per instance */
 #define CG_AMUL_IMPLICIT 2  /* e = H^H (H p) + (N0/Es) p, two matrix-vector products */
+/* CG least squares (Sec. III-E) in place of Algorithm 1: detection solves
+ * min || [y; 0] - [H; sqrt(N0/Es) I] x ||, precoding min || t - [H^H, sqrt(N0/Es) I] x ||
+ * with q = the first B entries of x, both by K CGLS iterations from x = 0,
+ * in FP32 on the CUDA cores whatever the precision field says, with no Gram.
+ * Detection keeps the approximate tracker (Eqs. 11-13) on CGLS's step sizes,
+ * which equal CG's in exact arithmetic; in precoding CGLS minimises the
+ * residual, so its iterates differ from CG-P's before K = U. Not with
+ * CG_SINR_EXACT (CG_ENOTSUP). For cg_detect, cg_precode and their host
+ * variants; the batched and serving entry points always form the Gram. */
+#define CG_AMUL_CGLS 3
 
 /* Arithmetic of the Gram H^H H and matched filter H^H y (CG itself is FP32). */
 #define CG_PREC_FP32 0
@@ -142,6 +152,33 @@ int cg_detect_host(const cg_params* p, int64_t n_inst, const void* H, const void
 int cg_precode_host(const cg_params* p, int64_t n_inst, const void* H, const void* T,
                     void* q, float* qnorm, int32_t normalize, int32_t* status,
                     void* stream);
+
+/* ------------------------------------------------------------------------
+ * Neumann-series detection and precoding (Sec. III-F), a comparator
+ * ------------------------------------------------------------------------ */
+
+/* Largest number of Neumann terms. */
+#define CG_NEUMANN_K_MAX 16
+
+/* The truncated K-term Neumann series of Sec. III-F,
+ *   A^-1 ~ sum_{k=0}^{K-1} (-D^-1 E)^k D^-1,  A = D + E,  D = diag(A),
+ * applied to b = H^H y (detection: x_hat) or to t (precoding: q = H v, with
+ * ||q|| and the optional normalisation of cg_precode), on the same Gram and
+ * tensor-core staging as CG. The series converges when A is strongly
+ * diagonally dominant (B >> U); K terms cost K - 1 products A v.
+ * Arguments, layouts, ownership and errors follow cg_detect / cg_precode,
+ * except:
+ *   K         number of terms, 1 <= K <= CG_NEUMANN_K_MAX (not bounded by U);
+ *   precision CG_PREC_BF16, CG_PREC_FP16, CG_PREC_BF16X3 or CG_PREC_FP16X3;
+ *             CG_PREC_FP32 returns CG_ENOTSUP;
+ *   sinr_mode and amul_mode are ignored; qam_bits must be valid but is unused;
+ *   detection writes x_hat only (required): the paper's soft outputs are
+ *   those of CG; status is written as 0. */
+int cg_neumann_detect(const cg_params* p, int64_t n_inst, const void* H, const void* Y,
+                      void* xhat, int32_t* status, void* stream);
+int cg_neumann_precode(const cg_params* p, int64_t n_inst, const void* H, const void* T,
+                       void* q, float* qnorm, int32_t normalize, int32_t* status,
+                       void* stream);
 
 /* ------------------------------------------------------------------------
  * Batched uneven problems (one plan, one CUDA-graph launch per run)

@@ -13,7 +13,8 @@ Gradient-based Soft-Output Detection and Precoding in Massive MIMO Systems"
   N0, Es   noise variance per complex entry and per-user symbol energy;
            the regulariser is rho_u^-1 = N0/Es (Eq. 2)
   A, G     regularised Gram H^H H + (N0/Es) I and Gram H^H H (Eq. 7, Sec. III-C)
-  K        number of CG iterations (Algorithm 1)
+  K        number of CG iterations (Algorithm 1), or of Neumann-series terms
+           (Sec. III-F, the comparator at the end of this module)
 
 The arithmetic is plain numpy in float64/complex128 with no blocking or
 fusion: a matmul is the only library primitive used as a step. Loops run over
@@ -460,3 +461,192 @@ def mmse_precode_exact(H: np.ndarray, t: np.ndarray, N0: float, Es: float) -> np
     U = Hd.shape[0]
     P = Hd.conj().T @ cholesky_inverse(Hd @ Hd.conj().T + (N0 / Es) * np.eye(U))
     return P @ np.asarray(t, np.complex128)
+
+
+# ----------------------------------------------------------------------------
+# Truncated Neumann series (Sec. III-F, approximate matrix inversion)
+# ----------------------------------------------------------------------------
+
+def neumann_inverse(A: np.ndarray, K: int) -> np.ndarray:
+    """The K-term Neumann approximation of A^-1 (Sec. III-F): with A = D + E,
+    D the diagonal of A and E the rest,
+        A^-1 ~ sum_{k=0}^{K-1} (-D^-1 E)^k D^-1,
+    formed as the matrix sum of its K terms (explicit powers)."""
+    A = np.asarray(A, dtype=np.complex128)
+    D = np.diag(np.diag(A))
+    E = A - D
+    Dinv = np.diag(1.0 / np.diag(A))
+    M = -Dinv @ E
+    term = Dinv.copy()          # k = 0: (-D^-1 E)^0 D^-1
+    total = term.copy()
+    for _ in range(1, K):
+        term = M @ term         # (-D^-1 E)^k D^-1
+        total = total + term
+    return total
+
+
+def neumann_detect_one(H: np.ndarray, y: np.ndarray, N0: float, Es: float, K: int) -> np.ndarray:
+    """x_hat = A~^-1 H^H y with the K-term Neumann inverse of A = H^H H + rho_u^-1 I
+    (Sec. III-F applied to the MMSE estimate of Eqs. 2-3)."""
+    A = regularised_gram(H, N0, Es)
+    return neumann_inverse(A, K) @ matched_filter(H, y)
+
+
+def neumann_detect(H: np.ndarray, Y: np.ndarray, N0: float, Es: float, K: int) -> dict:
+    """Neumann detection over a batch: H[n, B, U], Y[n, R, B] -> x_hat[n, R, U], status[n]
+    (always STATUS_OK)."""
+    H = np.asarray(H)
+    Y = np.asarray(Y)
+    n, _, U = H.shape
+    R = Y.shape[1]
+    x = np.zeros((n, R, U), np.complex128)
+    for i in range(n):
+        for r in range(R):
+            x[i, r] = neumann_detect_one(H[i], Y[i, r], N0, Es, K)
+    return {"x_hat": x, "status": np.zeros(n, np.int32)}
+
+
+def neumann_precode_one(H: np.ndarray, t: np.ndarray, N0: float, Es: float, K: int) -> dict:
+    """q = H_d^H A~^-1 t with the K-term Neumann inverse of A = H_d H_d^H + rho_d^-1 I
+    (Sec. III-F applied to the precoder of Eqs. 5-6)."""
+    Hd = np.asarray(H, dtype=np.complex128).conj().T
+    U = Hd.shape[0]
+    A = Hd @ Hd.conj().T + (N0 / Es) * np.eye(U)
+    q = Hd.conj().T @ (neumann_inverse(A, K) @ np.asarray(t, np.complex128))
+    qn = float(np.sqrt(np.sum(np.abs(q) ** 2)))
+    return {"q": q, "qnorm": qn, "s": q / qn if qn > 0 else np.zeros_like(q)}
+
+
+def neumann_precode(H: np.ndarray, T: np.ndarray, N0: float, Es: float, K: int) -> dict:
+    """Neumann precoding over a batch: H[n, B, U], T[n, R, U] -> q[n, R, B], qnorm[n, R],
+    s[n, R, B], status[n] (always STATUS_OK: the series has no breakdown)."""
+    H = np.asarray(H)
+    T = np.asarray(T)
+    n, Bn, U = H.shape
+    R = T.shape[1]
+    out = {"q": np.zeros((n, R, Bn), np.complex128), "qnorm": np.zeros((n, R)),
+           "s": np.zeros((n, R, Bn), np.complex128), "status": np.zeros(n, np.int32)}
+    for i in range(n):
+        for r in range(R):
+            o = neumann_precode_one(H[i], T[i, r], N0, Es, K)
+            out["q"][i, r] = o["q"]
+            out["qnorm"][i, r] = o["qnorm"]
+            out["s"][i, r] = o["s"]
+    return out
+
+
+# ----------------------------------------------------------------------------
+# CG least squares (Sec. III-E): no Gram matrix
+# ----------------------------------------------------------------------------
+
+def cgls(Hbar: np.ndarray, ybar: np.ndarray, K: int) -> dict:
+    """K iterations of CGLS [Paige and Saunders 1982] on min_x ||ybar - Hbar x||_2,
+    started at x = 0 (Sec. III-E). Per iteration:
+        q_k = Hbar p_k, alpha_k = gamma_{k-1} / ||q_k||^2, x_k = x_{k-1} + alpha_k p_k,
+        r_k = r_{k-1} - alpha_k q_k, s_k = Hbar^H r_k, gamma_k = ||s_k||^2,
+        beta_k = gamma_k / gamma_{k-1}, p_{k+1} = s_k + beta_k p_k,
+    with r_0 = ybar, s_0 = p_1 = Hbar^H ybar. Breakdown as for CG: if gamma_{k-1}
+    or ||q_k||^2 is not > 0 the iteration stops and x keeps its last value."""
+    Hbar = np.asarray(Hbar, dtype=np.complex128)
+    r = np.asarray(ybar, dtype=np.complex128).copy()
+    s = Hbar.conj().T @ r
+    p = s.copy()
+    x = np.zeros_like(s)
+    gamma = np.real(np.vdot(s, s))
+    alphas, betas = [], []
+    broke = False
+    for _k in range(1, K + 1):
+        if not gamma > 0:
+            broke = True
+            break
+        q = Hbar @ p
+        qq = np.real(np.vdot(q, q))
+        if not qq > 0:
+            broke = True
+            break
+        alpha = gamma / qq
+        x = x + alpha * p
+        r = r - alpha * q
+        s = Hbar.conj().T @ r
+        gamma_new = np.real(np.vdot(s, s))
+        beta = gamma_new / gamma
+        p = s + beta * p
+        gamma = gamma_new
+        alphas.append(alpha)
+        betas.append(beta)
+    return {"x": x, "alphas": alphas, "betas": betas, "breakdown": broke}
+
+
+def cgls_detect_one(H: np.ndarray, y: np.ndarray, N0: float, Es: float, K: int,
+                    qam_bits: int) -> dict:
+    """CGLS detection (Sec. III-E): x_hat = argmin ||ybar - Hbar x|| after K CGLS
+    iterations, with ybar = [y; 0_U] and Hbar = [H; sqrt(rho_u^-1) I_U]. The
+    approximate SINR tracker of Eqs. 11-13 is built in with CGLS's own step
+    sizes, then the LLRs of Eq. 4."""
+    H = np.asarray(H, dtype=np.complex128)
+    Bn, U = H.shape
+    Hbar = np.vstack([H, np.sqrt(N0 / Es) * np.eye(U)])
+    ybar = np.concatenate([np.asarray(y, np.complex128), np.zeros(U, np.complex128)])
+    ls = cgls(Hbar, ybar, K)
+    G = gram(H)
+    D = np.real(np.diag(G)) + N0 / Es
+    l = approx_tracker_l(ls["alphas"], ls["betas"], D)
+    mu, nu2, rho = approx_tracker_sinr(l, np.real(np.diag(G)), N0)
+    llr, flag = maxlog_llr(ls["x"], mu, rho, qam_bits, Es)
+    status = (STATUS_BREAKDOWN if ls["breakdown"] else STATUS_OK) | flag
+    return {"x_hat": ls["x"], "mu": mu, "nu2": nu2, "rho": rho, "llr": llr, "status": status,
+            "alphas": ls["alphas"], "betas": ls["betas"]}
+
+
+def cgls_detect(H: np.ndarray, Y: np.ndarray, N0: float, Es: float, K: int,
+                qam_bits: int) -> dict:
+    """CGLS detection over a batch, in the layout of cg_detect."""
+    H = np.asarray(H)
+    Y = np.asarray(Y)
+    n, _, U = H.shape
+    R = Y.shape[1]
+    q = int(qam_bits)
+    out = {"x_hat": np.zeros((n, R, U), np.complex128), "mu": np.zeros((n, R, U)),
+           "rho": np.zeros((n, R, U)), "llr": np.zeros((n, R, U, q)),
+           "status": np.zeros(n, np.int32)}
+    for t in range(n):
+        for r in range(R):
+            o = cgls_detect_one(H[t], Y[t, r], N0, Es, K, q)
+            out["x_hat"][t, r] = o["x_hat"]
+            out["mu"][t, r] = o["mu"]
+            out["rho"][t, r] = o["rho"]
+            out["llr"][t, r] = o["llr"]
+            out["status"][t] |= o["status"]
+    return out
+
+
+def cgls_precode_one(H: np.ndarray, t: np.ndarray, N0: float, Es: float, K: int) -> dict:
+    """CGLS precoding (Sec. III-E): qbar = argmin ||t - Hbar_d qtilde|| after K CGLS
+    iterations with Hbar_d = [H_d, sqrt(rho_d^-1) I_U], H_d = H_u^H; q is the first
+    B entries of qbar, and s = q / ||q||."""
+    H = np.asarray(H, dtype=np.complex128)
+    Bn, U = H.shape
+    Hbar_d = np.hstack([H.conj().T, np.sqrt(N0 / Es) * np.eye(U)])
+    ls = cgls(Hbar_d, np.asarray(t, np.complex128), K)
+    q = ls["x"][:Bn]
+    qn = float(np.sqrt(np.sum(np.abs(q) ** 2)))
+    return {"q": q, "qnorm": qn, "s": q / qn if qn > 0 else np.zeros_like(q),
+            "status": STATUS_BREAKDOWN if ls["breakdown"] else STATUS_OK}
+
+
+def cgls_precode(H: np.ndarray, T: np.ndarray, N0: float, Es: float, K: int) -> dict:
+    """CGLS precoding over a batch, in the layout of cg_precode."""
+    H = np.asarray(H)
+    T = np.asarray(T)
+    n, Bn, U = H.shape
+    R = T.shape[1]
+    out = {"q": np.zeros((n, R, Bn), np.complex128), "qnorm": np.zeros((n, R)),
+           "s": np.zeros((n, R, Bn), np.complex128), "status": np.zeros(n, np.int32)}
+    for i in range(n):
+        for r in range(R):
+            o = cgls_precode_one(H[i], T[i, r], N0, Es, K)
+            out["q"][i, r] = o["q"]
+            out["qnorm"][i, r] = o["qnorm"]
+            out["s"][i, r] = o["s"]
+            out["status"][i] |= o["status"]
+    return out

@@ -1,8 +1,9 @@
 """Thin ctypes binding of libcgmimo (include/cgmimo.h).
 
 The functions cg_detect, cg_precode, cg_detect_host, cg_precode_host,
-cg_release_workspace, cg_strerror and cg_version have the names and argument
-order of the C ABI. detect() and precode() are conveniences that allocate the
+cg_neumann_detect, cg_neumann_precode, cg_release_workspace, cg_strerror and
+cg_version have the names and argument order of the C ABI. detect(),
+precode(), neumann_detect() and neumann_precode() are conveniences that allocate the
 outputs as torch tensors and marshal pointers; every step of the computation
 runs in the CUDA library. There is no fallback: if the library is missing
 the first call raises.
@@ -82,6 +83,9 @@ _SIGS = {
                        _VP, _VP],
     "cg_precode_host": [ctypes.POINTER(CgParams), ctypes.c_int64, _VP, _VP, _VP, _VP,
                         ctypes.c_int32, _VP, _VP],
+    "cg_neumann_detect": [ctypes.POINTER(CgParams), ctypes.c_int64, _VP, _VP, _VP, _VP, _VP],
+    "cg_neumann_precode": [ctypes.POINTER(CgParams), ctypes.c_int64, _VP, _VP, _VP, _VP,
+                           ctypes.c_int32, _VP, _VP],
     "cg_release_workspace": [],
     "cg_plan_create": [ctypes.POINTER(CgDesc), ctypes.c_int64, ctypes.c_int32, _VP,
                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)],
@@ -168,6 +172,18 @@ def cg_precode(p: CgParams, n_inst, H, T, q, qnorm=None, normalize=0, status=Non
                stream=None) -> int:
     return library().cg_precode(ctypes.byref(p), int(n_inst), _ptr(H), _ptr(T), _ptr(q),
                                 _ptr(qnorm), int(normalize), _ptr(status), _stream(stream))
+
+
+def cg_neumann_detect(p: CgParams, n_inst, H, Y, xhat, status=None, stream=None) -> int:
+    return library().cg_neumann_detect(ctypes.byref(p), int(n_inst), _ptr(H), _ptr(Y),
+                                       _ptr(xhat), _ptr(status), _stream(stream))
+
+
+def cg_neumann_precode(p: CgParams, n_inst, H, T, q, qnorm=None, normalize=0, status=None,
+                       stream=None) -> int:
+    return library().cg_neumann_precode(ctypes.byref(p), int(n_inst), _ptr(H), _ptr(T), _ptr(q),
+                                        _ptr(qnorm), int(normalize), _ptr(status),
+                                        _stream(stream))
 
 
 def cg_detect_host(p: CgParams, n_inst, H, Y, xhat=None, mu=None, rho=None, llr=None,
@@ -300,4 +316,34 @@ def precode(H, T, N0, K, Es=1.0, normalize=False, amul_mode=0, precision=0, stre
     p = params(B, U, 2, K, R, N0, Es, 0, amul_mode, precision)
     _check(cg_precode(p, n, H, T, out["q"], out["qnorm"], int(bool(normalize)), out["status"],
                       stream), "cg_precode")
+    return out
+
+
+def neumann_detect(H, Y, N0, K, Es=1.0, precision=4, stream=None) -> dict:
+    """Neumann-series x_hat (Sec. III-F) on device tensors H[n, B, U], Y[n, R, B]."""
+    import torch
+    n, B, U = H.shape
+    R = Y.shape[1]
+    assert Y.shape == (n, R, B) and H.is_contiguous() and Y.is_contiguous()
+    dev = H.device
+    out = {"xhat": torch.empty((n, R, U), dtype=torch.complex64, device=dev),
+           "status": torch.empty((n,), dtype=torch.int32, device=dev)}
+    p = params(B, U, 2, K, R, N0, Es, 0, 0, precision)
+    _check(cg_neumann_detect(p, n, H, Y, out["xhat"], out["status"], stream), "cg_neumann_detect")
+    return out
+
+
+def neumann_precode(H, T, N0, K, Es=1.0, normalize=False, precision=4, stream=None) -> dict:
+    """Neumann-series precoding q = H v (Sec. III-F) on device tensors H[n, B, U], T[n, R, U]."""
+    import torch
+    n, B, U = H.shape
+    R = T.shape[1]
+    assert T.shape == (n, R, U) and H.is_contiguous() and T.is_contiguous()
+    dev = H.device
+    out = {"q": torch.empty((n, R, B), dtype=torch.complex64, device=dev),
+           "qnorm": torch.empty((n, R), dtype=torch.float32, device=dev),
+           "status": torch.empty((n,), dtype=torch.int32, device=dev)}
+    p = params(B, U, 2, K, R, N0, Es, 0, 0, precision)
+    _check(cg_neumann_precode(p, n, H, T, out["q"], out["qnorm"], int(bool(normalize)),
+                              out["status"], stream), "cg_neumann_precode")
     return out

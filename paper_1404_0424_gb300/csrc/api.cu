@@ -50,7 +50,9 @@ namespace {
 // Modes implemented by this build: the exact tracker needs the Gram, so it
 // does not combine with the implicit product.
 int check_supported(const cg_params* p) {
-  if (p->amul_mode == CG_AMUL_IMPLICIT && p->sinr_mode == CG_SINR_EXACT) return CG_ENOTSUP;
+  if ((p->amul_mode == CG_AMUL_IMPLICIT || p->amul_mode == CG_AMUL_CGLS) &&
+      p->sinr_mode == CG_SINR_EXACT)
+    return CG_ENOTSUP;
   return CG_OK;
 }
 
@@ -82,8 +84,10 @@ int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void*
   a.exact = p->sinr_mode == CG_SINR_EXACT;
   a.bulk = (p->B % 2 == 0) && aligned(H, 16) && aligned(Y, 16);
   cudaError_t err;
-  if (use_implicit(p->amul_mode, p->precision, p->K, p->R, p->U, a.exact)) {
-    err = launch_detect_implicit(padded_users(p->U), a, s);
+  if (p->amul_mode == CG_AMUL_CGLS) {
+    err = launch_detect_implicit(padded_users(p->U), a, s, true);
+  } else if (use_implicit(p->amul_mode, p->precision, p->K, p->R, p->U, a.exact)) {
+    err = launch_detect_implicit(padded_users(p->U), a, s, false);
   } else if (p->precision == CG_PREC_FP32) {
     err = launch_detect(padded_users(p->U), a, s, nullptr);
   } else {
@@ -118,8 +122,10 @@ int precode_device(const cg_params* p, int64_t n_inst, const void* H, const void
   a.bulk_h = ((p->B * p->U) % 2 == 0) && aligned(H, 16);
   a.bulk_t = ((p->R * p->U) % 2 == 0) && aligned(T, 16);
   cudaError_t err;
-  if (use_implicit(p->amul_mode, p->precision, p->K, p->R, p->U, false)) {
-    err = launch_precode_implicit(padded_users(p->U), a, s);
+  if (p->amul_mode == CG_AMUL_CGLS) {
+    err = launch_precode_implicit(padded_users(p->U), a, s, true);
+  } else if (use_implicit(p->amul_mode, p->precision, p->K, p->R, p->U, false)) {
+    err = launch_precode_implicit(padded_users(p->U), a, s, false);
   } else if (p->precision == CG_PREC_FP32) {
     err = launch_precode(padded_users(p->U), a, s, nullptr);
   } else {
@@ -219,6 +225,88 @@ int cg_precode(const cg_params* p, int64_t n_inst, const void* H, const void* T,
   if ((rc = check_supported(p)) != CG_OK) return rc;
   return precode_device(p, n_inst, H, T, q, qnorm, normalize, status,
                         static_cast<cudaStream_t>(stream));
+}
+
+namespace {
+
+// Checks shared by the Neumann entry points: K terms in [1, CG_NEUMANN_K_MAX]
+// and a tensor-core precision; the shape and pointer checks are those of CG
+// (with K = 1, since the series has no K <= U bound).
+int check_neumann(const cg_params* p, cg_params* shape) {
+  if (p == nullptr) return CG_EINVAL;
+  if (p->K < 1 || p->K > CG_NEUMANN_K_MAX) return CG_EINVAL;
+  if (p->precision == CG_PREC_FP32) return CG_ENOTSUP;
+  if (p->precision < CG_PREC_BF16 || p->precision > CG_PREC_FP16X3) return CG_EINVAL;
+  *shape = *p;
+  shape->K = 1;
+  shape->sinr_mode = CG_SINR_APPROX;
+  shape->amul_mode = CG_AMUL_EXPLICIT;
+  return CG_OK;
+}
+
+}  // namespace
+
+int cg_neumann_detect(const cg_params* p, int64_t n_inst, const void* H, const void* Y,
+                      void* xhat, int32_t* status, void* stream) {
+  cg_params shape;
+  int rc = check_neumann(p, &shape);
+  if (rc != CG_OK) return rc;
+  if (xhat == nullptr) return CG_EINVAL;
+  rc = check_detect(&shape, n_inst, H, Y, xhat, nullptr, nullptr, nullptr, status);
+  if (rc != CG_OK || n_inst == 0) return rc;
+  DetectArgs a{};
+  a.H = static_cast<const float2*>(H);
+  a.Y = static_cast<const float2*>(Y);
+  a.xhat = static_cast<float2*>(xhat);
+  a.status = status;
+  a.n_inst = n_inst;
+  a.B = p->B;
+  a.U = p->U;
+  a.R = p->R;
+  a.K = p->K;
+  a.q = p->qam_bits;
+  a.N0 = p->N0;
+  a.Es = p->Es;
+  a.sigma = p->N0 / p->Es;
+  a.bulk = (p->B % 2 == 0) && aligned(H, 16) && aligned(Y, 16);
+  int el;
+  bool x3;
+  tc_mode(p->precision, &el, &x3);
+  const cudaError_t err =
+      launch_neumann_detect(padded_users(p->U), el, x3, a, static_cast<cudaStream_t>(stream));
+  if (err == cudaErrorInvalidValue) return CG_EINVAL;
+  return err == cudaSuccess ? CG_OK : CG_ECUDA;
+}
+
+int cg_neumann_precode(const cg_params* p, int64_t n_inst, const void* H, const void* T, void* q,
+                       float* qnorm, int32_t normalize, int32_t* status, void* stream) {
+  cg_params shape;
+  int rc = check_neumann(p, &shape);
+  if (rc != CG_OK) return rc;
+  rc = check_precode(&shape, n_inst, H, T, q, qnorm, status);
+  if (rc != CG_OK || n_inst == 0) return rc;
+  PrecodeArgs a{};
+  a.H = static_cast<const float2*>(H);
+  a.T = static_cast<const float2*>(T);
+  a.q = static_cast<float2*>(q);
+  a.qnorm = qnorm;
+  a.status = status;
+  a.n_inst = n_inst;
+  a.B = p->B;
+  a.U = p->U;
+  a.R = p->R;
+  a.K = p->K;
+  a.sigma = p->N0 / p->Es;
+  a.normalize = normalize != 0;
+  a.bulk_h = ((p->B * p->U) % 2 == 0) && aligned(H, 16);
+  a.bulk_t = ((p->R * p->U) % 2 == 0) && aligned(T, 16);
+  int el;
+  bool x3;
+  tc_mode(p->precision, &el, &x3);
+  const cudaError_t err =
+      launch_neumann_precode(padded_users(p->U), el, x3, a, static_cast<cudaStream_t>(stream));
+  if (err == cudaErrorInvalidValue) return CG_EINVAL;
+  return err == cudaSuccess ? CG_OK : CG_ECUDA;
 }
 
 int cg_detect_host(const cg_params* p, int64_t n_inst, const void* H, const void* Y, void* xhat,

@@ -526,6 +526,47 @@ struct WarpCg {
     }
   }
 
+  // Sec. III-F: the K-term Neumann series x = sum_{k<K} (-D^-1 E)^k D^-1 b
+  // with A = D + E, D = diag(A), evaluated as its partial sums
+  //   S_1 = D^-1 b,  S_{k+1} = S_k + D^-1 (b - A S_k)
+  // (S_{k+1} = D^-1 b - D^-1 E S_k). res holds b on entry; v gets S_K. Rows
+  // with a zero b (rows >= R) stay zero.
+  __device__ __forceinline__ void neumann(const uint2* frag, int K) {
+    float id[NB][2];
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) id[nt][c] = 1.f / D[nt][c];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      broke[h] = false;
+#pragma unroll
+      for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          v[h][nt][c] = make_float2(res[h][nt][c].x * id[nt][c], res[h][nt][c].y * id[nt][c]);
+    }
+    for (int k = 2; k <= K; ++k) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) p[h][nt][c] = v[h][nt][c];
+      float Er[NB][4], Ei[NB][4];
+      matvec(frag, Er, Ei);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            v[h][nt][c].x = fmaf(res[h][nt][c].x - Er[nt][2 * h + c], id[nt][c], v[h][nt][c].x);
+            v[h][nt][c].y = fmaf(res[h][nt][c].y - Ei[nt][2 * h + c], id[nt][c], v[h][nt][c].y);
+          }
+    }
+  }
+
   // Eq. 11 with A replaced by D (scalar per position) from the recorded
   // alpha_k, beta_k: l_1 = alpha_1, and for k >= 2
   //   l_k = l_{k-1} + (alpha_k (1 + beta_{k-1}) / alpha_{k-1} - alpha_k D)(l_{k-1} - l_{k-2})
@@ -769,7 +810,11 @@ __device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int 
 }
 
 // Lines 7-19 and Eq. 4 of one instance whose Gram and matched filters are done.
-template <int UT, int EL, bool VEC>
+// Solvers of the warp bodies: CG (Algorithm 1) or the Neumann series (Sec. III-F).
+constexpr int SOLVE_CG = 0;
+constexpr int SOLVE_NEUMANN = 1;
+
+template <int UT, int EL, bool VEC, int SOLVER = SOLVE_CG>
 __device__ __forceinline__ int detect_warp_finish(const DetItem& it, uint2* frag, float2* sAB,
                                                   const GramAcc<UT>& Gr, const GramAcc<UT>& Gi,
                                                   const VecAcc<UT>& Mr, const VecAcc<UT>& Mn) {
@@ -786,6 +831,25 @@ __device__ __forceinline__ int detect_warp_finish(const DetItem& it, uint2* frag
       for (int c = 0; c < 2; ++c)
         cg.res[hh][nt][c] = make_float2(Mr[nt][2 * hh + c], -Mn[nt][2 * hh + c]);
   __syncwarp();
+  if constexpr (SOLVER == SOLVE_NEUMANN) {
+    // x_hat only: the soft outputs of this path are those of CG
+    cg.neumann(frag, it.K);
+    float one[NB][2], zero[NB][2];
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        one[nt][c] = 1.f;
+        zero[nt][c] = 0.f;
+      }
+    int nflags = 0;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh)
+      if (g + 8 * hh < it.R) store_row_detect<UT, 2, VEC>(it, g + 8 * hh, t, cg.v[hh], one, zero,
+                                                          0.f, &nflags);
+    if (lane == 0 && it.status) *it.status = 0;
+    return 0;
+  }
   cg.template run<true>(frag, sAB, it.R, it.K);
   __syncwarp();
 
@@ -842,7 +906,7 @@ __device__ __forceinline__ int64_t warp_next_early(const S& s, int64_t cur, int6
 
 // Instance loop: the Gram of an instance, then the next instance's first
 // load stages, then the CG and outputs (which overlap those loads).
-template <int UT, int EL, bool X3, class Src>
+template <int UT, int EL, bool X3, class Src, int SOLVER = SOLVE_CG>
 __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* mine) {
   constexpr int NB = UT / 8;
   const int warp = threadIdx.x >> 5;
@@ -877,8 +941,8 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
     int st;
     {
       const DetItem it = det_item(src, cur);
-      st = vec ? detect_warp_finish<UT, EL, true>(it, frag, sAB, Gr, Gi, Mr, Mn)
-               : detect_warp_finish<UT, EL, false>(it, frag, sAB, Gr, Gi, Mr, Mn);
+      st = vec ? detect_warp_finish<UT, EL, true, SOLVER>(it, frag, sAB, Gr, Gi, Mr, Mn)
+               : detect_warp_finish<UT, EL, false, SOLVER>(it, frag, sAB, Gr, Gi, Mr, Mn);
     }
     __syncwarp();
     if constexpr (SrcTraits<Src>::kDyn) {
@@ -904,7 +968,7 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
 
 // Lines 7-14 with b = t, ||q||, then line 20 (q = H v) of one instance whose
 // Gram is done.
-template <int UT, int EL, bool X3, bool VEC>
+template <int UT, int EL, bool X3, bool VEC, int SOLVER = SOLVE_CG>
 __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* frag,
                                                    const GramAcc<UT>& Gr, const GramAcc<UT>& Gi) {
   constexpr int NB = UT / 8;
@@ -925,7 +989,10 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
       }
   }
   __syncwarp();
-  cg.template run<false>(frag, nullptr, it.R, it.K);
+  if constexpr (SOLVER == SOLVE_NEUMANN)
+    cg.neumann(frag, it.K);
+  else
+    cg.template run<false>(frag, nullptr, it.R, it.K);
 
   // ||q||^2 = v^H (A - sigma I) v with one more product w = A v
 #pragma unroll
@@ -1055,7 +1122,7 @@ __device__ __forceinline__ bool precode_vec(const PreItem& it) {
 
 // Instance loop. CG-P reads H twice (Gram, then q = H v); both passes use
 // 16-byte register loads through L1, where the second pass finds part of H.
-template <int UT, int EL, bool X3, class Src>
+template <int UT, int EL, bool X3, class Src, int SOLVER = SOLVE_CG>
 __device__ __forceinline__ void precode_warp_body(const Src& src, unsigned char* mine) {
   constexpr int NB = UT / 8;
   const int warp = threadIdx.x >> 5;
@@ -1069,11 +1136,11 @@ __device__ __forceinline__ void precode_warp_body(const Src& src, unsigned char*
     int st;
     if (precode_vec<UT>(it)) {
       warp_gram<UT, EL, X3, LD_VEC, false>(it.H, nullptr, it.B, it.U, 0, nullptr, Gr, Gi, Mr, Mn);
-      st = precode_warp_finish<UT, EL, X3, true>(it, frag, Gr, Gi);
+      st = precode_warp_finish<UT, EL, X3, true, SOLVER>(it, frag, Gr, Gi);
     } else {
       warp_gram<UT, EL, X3, LD_ELEM, false>(it.H, nullptr, it.B, it.U, 0, nullptr, Gr, Gi, Mr,
                                             Mn);
-      st = precode_warp_finish<UT, EL, X3, false>(it, frag, Gr, Gi);
+      st = precode_warp_finish<UT, EL, X3, false, SOLVER>(it, frag, Gr, Gi);
     }
     __syncwarp();
     if constexpr (SrcTraits<Src>::kDyn) {

@@ -18,7 +18,7 @@ inline int check_common(const cg_params* p, int64_t n_inst) {
   if (p->K < 1 || p->K > p->U || p->K > CG_K_MAX) return CG_EINVAL;
   if (!(p->N0 > 0.f) || !std::isfinite(p->N0)) return CG_EINVAL;
   if (!(p->Es > 0.f) || !std::isfinite(p->Es)) return CG_EINVAL;
-  if (p->amul_mode < CG_AMUL_AUTO || p->amul_mode > CG_AMUL_IMPLICIT) return CG_EINVAL;
+  if (p->amul_mode < CG_AMUL_AUTO || p->amul_mode > CG_AMUL_CGLS) return CG_EINVAL;
   if (p->precision < CG_PREC_FP32 || p->precision > CG_PREC_FP16X3) return CG_EINVAL;
   return CG_OK;
 }

@@ -1,4 +1,5 @@
-// Launchers of the implicit-product FP32 kernels (cg_implicit.cuh).
+// Launchers of the implicit-product FP32 kernels and their CGLS variants
+// (cg_implicit.cuh).
 #include <mutex>
 #include <unordered_map>
 
@@ -49,46 +50,50 @@ cudaError_t launch_one(Kern kern, uint64_t id, int nthr, uint32_t smem, int64_t 
   return cudaSuccess;
 }
 
-template <int UT>
+template <int UT, bool CGLS>
 cudaError_t det(const DetectArgs& a, cudaStream_t s) {
   constexpr int NTHR = TileCfg<UT>::NTHR;
-  const uint32_t smem = implicit_plan<UT>(a.B, a.U, a.R, true).total;
+  const uint32_t smem = implicit_plan<UT>(a.B, a.U, a.R, true, CGLS).total;
   int grid = 0;
-  cudaError_t err = launch_one(detect_implicit_kernel<UT>, 0x100 | UT, NTHR, smem, a.n_inst, &grid);
+  const uint64_t id = (CGLS ? 0x300 : 0x100) | UT;
+  cudaError_t err =
+      launch_one(detect_implicit_kernel<UT, CGLS>, id, NTHR, smem, a.n_inst, &grid);
   if (err != cudaSuccess) return err;
-  detect_implicit_kernel<UT><<<unsigned(grid), NTHR, smem, s>>>(a);
+  detect_implicit_kernel<UT, CGLS><<<unsigned(grid), NTHR, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int UT>
+template <int UT, bool CGLS>
 cudaError_t pre(const PrecodeArgs& a, cudaStream_t s) {
   constexpr int NTHR = TileCfg<UT>::NTHR;
-  const uint32_t smem = implicit_plan<UT>(a.B, a.U, a.R, false).total;
+  const uint32_t smem = implicit_plan<UT>(a.B, a.U, a.R, false, CGLS).total;
   int grid = 0;
-  cudaError_t err = launch_one(precode_implicit_kernel<UT>, 0x200 | UT, NTHR, smem, a.n_inst, &grid);
+  const uint64_t id = (CGLS ? 0x400 : 0x200) | UT;
+  cudaError_t err =
+      launch_one(precode_implicit_kernel<UT, CGLS>, id, NTHR, smem, a.n_inst, &grid);
   if (err != cudaSuccess) return err;
-  precode_implicit_kernel<UT><<<unsigned(grid), NTHR, smem, s>>>(a);
+  precode_implicit_kernel<UT, CGLS><<<unsigned(grid), NTHR, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_detect_implicit(int UT, const DetectArgs& a, cudaStream_t s) {
+cudaError_t launch_detect_implicit(int UT, const DetectArgs& a, cudaStream_t s, bool cgls) {
   switch (UT) {
-    case 4: return det<4>(a, s);
-    case 8: return det<8>(a, s);
-    case 16: return det<16>(a, s);
-    case 32: return det<32>(a, s);
+    case 4: return cgls ? det<4, true>(a, s) : det<4, false>(a, s);
+    case 8: return cgls ? det<8, true>(a, s) : det<8, false>(a, s);
+    case 16: return cgls ? det<16, true>(a, s) : det<16, false>(a, s);
+    case 32: return cgls ? det<32, true>(a, s) : det<32, false>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_precode_implicit(int UT, const PrecodeArgs& a, cudaStream_t s) {
+cudaError_t launch_precode_implicit(int UT, const PrecodeArgs& a, cudaStream_t s, bool cgls) {
   switch (UT) {
-    case 4: return pre<4>(a, s);
-    case 8: return pre<8>(a, s);
-    case 16: return pre<16>(a, s);
-    case 32: return pre<32>(a, s);
+    case 4: return cgls ? pre<4, true>(a, s) : pre<4, false>(a, s);
+    case 8: return cgls ? pre<8, true>(a, s) : pre<8, false>(a, s);
+    case 16: return cgls ? pre<16, true>(a, s) : pre<16, false>(a, s);
+    case 32: return cgls ? pre<32, true>(a, s) : pre<32, false>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -56,6 +56,9 @@ cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const Ba
 // tracker only. Batch and serve forms as above (grid in CTAs of 4 warps).
 cudaError_t launch_detect_warp(int UT, int el, bool x3, const DetectArgs& a, cudaStream_t s);
 cudaError_t launch_precode_warp(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s);
+// Neumann-series variants of the warp kernels (neumann.cu), Sec. III-F.
+cudaError_t launch_neumann_detect(int UT, int el, bool x3, const DetectArgs& a, cudaStream_t s);
+cudaError_t launch_neumann_precode(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s);
 cudaError_t launch_batch_warp(int op, int UT, int el, bool x3, const BatchArgs& b, int max_grid,
                               cudaStream_t s, bool launch, int* grid_out);
 // Serving kernels (serve_kernels.cu): the warp kernel of the six
@@ -67,9 +70,10 @@ cudaError_t launch_serve_warp(int el, bool x3, const ServeArgs& sa, int grid, cu
 cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
                             cudaStream_t st, bool launch, int* resident_out);
 
-// Implicit-product FP32 kernels (implicit.cu): e = H^H (H p) + sigma p.
-cudaError_t launch_detect_implicit(int UT, const DetectArgs& a, cudaStream_t s);
-cudaError_t launch_precode_implicit(int UT, const PrecodeArgs& a, cudaStream_t s);
+// Implicit-product FP32 kernels (implicit.cu): e = H^H (H p) + sigma p; with
+// cgls = true, CG least squares on the augmented systems (Sec. III-E).
+cudaError_t launch_detect_implicit(int UT, const DetectArgs& a, cudaStream_t s, bool cgls);
+cudaError_t launch_precode_implicit(int UT, const PrecodeArgs& a, cudaStream_t s, bool cgls);
 
 // Whether A p is applied implicitly for these parameters: requested, or
 // CG_AMUL_AUTO on the FP32 path when the two products per iteration cost

@@ -412,6 +412,117 @@ def test_exact_convergence_stops_the_iteration():
 
 
 # ---------------------------------------------------------------------------
+# Truncated Neumann series (Sec. III-F)
+# ---------------------------------------------------------------------------
+
+def test_golden_neumann2(golden):
+    g = {k.split(".", 1)[1]: v for k, v in golden.items() if k.startswith("neumann2.")}
+    H = np.array(g["H"], complex)
+    y = np.array(g["y"], complex)
+    t = np.array(g["t"], complex)
+    for K in (1, 2, 3):
+        np.testing.assert_allclose(orc.neumann_detect_one(H, y, g["N0"], g["Es"], K),
+                                   g[f"xhat_K{K}"], atol=1e-15)
+    for K in (1, 2):
+        np.testing.assert_allclose(orc.neumann_precode_one(H, t, g["N0"], g["Es"], K)["q"],
+                                   g[f"q_K{K}"], atol=1e-15)
+    # the series converges to the exact MMSE estimate (spectral radius of M is 1/sqrt(6))
+    np.testing.assert_allclose(orc.neumann_detect_one(H, y, g["N0"], g["Es"], 60),
+                               g["xhat_exact"], atol=1e-14)
+
+
+def test_neumann_is_exact_for_a_diagonal_gram():
+    # orthogonal columns: E = 0, so every K gives A^-1 b
+    Q, _ = np.linalg.qr(crandn(RNG, 16, 4))
+    H = Q * np.array([0.5, 1.0, 2.0, 3.0])
+    y = crandn(RNG, 16)
+    ex = orc.mmse_exact(H, y, 0.4, 1.0)["x_hat"]
+    for K in (1, 2, 5):
+        np.testing.assert_allclose(orc.neumann_detect_one(H, y, 0.4, 1.0, K), ex, rtol=1e-12)
+
+
+@pytest.mark.parametrize("B,U", [(64, 4), (128, 8), (256, 16)])
+def test_neumann_converges_to_mmse_when_diagonally_dominant(B, U):
+    H = crandn(RNG, B, U)
+    y = crandn(RNG, B)
+    t = crandn(RNG, U)
+    N0 = U / 10.0
+    ex = orc.mmse_exact(H, y, N0, 1.0)["x_hat"]
+    errs = [relerr(orc.neumann_detect_one(H, y, N0, 1.0, K), ex) for K in (1, 2, 3, 4)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs   # monotone for B >> U
+    assert relerr(orc.neumann_detect_one(H, y, N0, 1.0, 60), ex) < 1e-10
+    assert relerr(orc.neumann_precode_one(H, t, N0, 1.0, 60)["q"],
+                  orc.mmse_precode_exact(H, t, N0, 1.0)) < 1e-10
+
+
+def test_neumann_partial_sums_follow_the_jacobi_recursion():
+    # sum_{k<K} (-D^-1 E)^k D^-1 b equals K steps of x <- D^-1 (b - E x) from x = 0,
+    # computed here with vectors only (no matrix powers)
+    H = crandn(RNG, 48, 6)
+    y = crandn(RNG, 48)
+    A = orc.regularised_gram(H, 0.5, 1.0)
+    b = H.conj().T @ y
+    d = np.array([A[i, i] for i in range(6)])
+    x = np.zeros(6, complex)
+    for K in range(1, 7):
+        Ex = np.array([sum(A[i, j] * x[j] for j in range(6) if j != i) for i in range(6)])
+        x = (b - Ex) / d
+        np.testing.assert_allclose(orc.neumann_detect_one(H, y, 0.5, 1.0, K), x, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# CG least squares (Sec. III-E)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("B,U,K", [(16, 4, 1), (32, 8, 3), (64, 8, 5), (128, 16, 3)])
+def test_cgls_detection_iterates_equal_cg(B, U, K):
+    # in exact arithmetic CGLS on [H; sqrt(sigma) I] runs CG on the normal equations
+    # A x = H^H y: same iterate, same step sizes (a different algorithm, so an identity)
+    H = crandn(RNG, B, U)
+    y = crandn(RNG, B)
+    N0 = U / 10.0
+    o = orc.cgls_detect_one(H, y, N0, 1.0, K, 4)
+    cg = orc.cg_detect_one(H, y, N0, 1.0, K, 4, "approx")
+    assert relerr(o["x_hat"], cg["x_hat"]) < 1e-9
+    np.testing.assert_allclose(o["alphas"], cg["alphas"], rtol=1e-9)
+    np.testing.assert_allclose(o["betas"], cg["betas"], rtol=1e-8)
+    np.testing.assert_allclose(o["mu"], cg["mu"], rtol=1e-9)
+
+
+@pytest.mark.parametrize("B,U", [(8, 2), (32, 8), (64, 13)])
+def test_cgls_is_exact_at_K_equals_U(B, U):
+    H = crandn(RNG, B, U)
+    y = crandn(RNG, B)
+    t = crandn(RNG, U)
+    N0 = U / 5.0
+    assert relerr(orc.cgls_detect_one(H, y, N0, 1.0, U, 2)["x_hat"],
+                  orc.mmse_exact(H, y, N0, 1.0)["x_hat"]) < 1e-9
+    assert relerr(orc.cgls_precode_one(H, t, N0, 1.0, U)["q"],
+                  orc.mmse_precode_exact(H, t, N0, 1.0)) < 1e-9
+
+
+def test_golden_cgls_precode_K1(golden):
+    g = {k.split(".", 1)[1]: v for k, v in golden.items() if k.startswith("diag2.")}
+    c = {k.split(".", 1)[1]: v for k, v in golden.items() if k.startswith("cgls_diag2.")}
+    o = orc.cgls_precode_one(np.array(g["H"], complex), np.array(g["t"], complex),
+                             g["N0"], g["Es"], 1)
+    np.testing.assert_allclose(o["q"], c["q_K1"], atol=1e-15)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_cgls_precoding_minimises_the_residual_over_the_krylov_space(K):
+    # qbar_K = Hbar_d^H z with z = argmin over span{t, A t, .., A^(K-1) t} of ||t - A z||
+    # (a least-squares solve on an explicit Krylov basis), so q_K = H z
+    H = crandn(RNG, 48, 6)
+    t = crandn(RNG, 6)
+    N0 = 0.6
+    A = orc.regularised_gram(H, N0, 1.0)
+    basis = np.stack([np.linalg.matrix_power(A, j) @ t for j in range(K)], axis=1)
+    c, *_ = np.linalg.lstsq(A @ basis, t, rcond=None)
+    assert relerr(orc.cgls_precode_one(H, t, N0, 1.0, K)["q"], H @ (basis @ c)) < 1e-9
+
+
+# ---------------------------------------------------------------------------
 # The pins catch planted mistakes (each mistake is planted in the oracle)
 # ---------------------------------------------------------------------------
 
@@ -456,3 +567,43 @@ def test_planted_dropped_interference_is_caught(monkeypatch):
     _plant(monkeypatch, "exact_tracker_sinr", no_interf)
     with pytest.raises(AssertionError):
         test_exact_tracker_at_K_equals_U_matches_mmse(32, 8)
+
+
+def test_planted_neumann_sign_is_caught(monkeypatch, golden):
+    import oracle.cgmimo_oracle as mod
+
+    def plus_sign(A, K):
+        A = np.asarray(A, complex)
+        Dinv = np.diag(1.0 / np.diag(A))
+        M = Dinv @ (A - np.diag(np.diag(A)))
+        term, total = Dinv.copy(), Dinv.copy()
+        for _ in range(1, K):
+            term = M @ term
+            total = total + term
+        return total
+    _plant(monkeypatch, "neumann_inverse", plus_sign)
+    with pytest.raises(AssertionError):
+        test_golden_neumann2(golden)
+
+
+def test_planted_cgls_steepest_descent_is_caught(monkeypatch):
+    import oracle.cgmimo_oracle as mod
+    orig = mod.cgls
+
+    def no_beta(Hbar, ybar, K):
+        Hbar = np.asarray(Hbar, complex)
+        x = np.zeros(Hbar.shape[1], complex)
+        r = np.asarray(ybar, complex).copy()
+        alphas, betas = [], []
+        for _ in range(K):
+            s = Hbar.conj().T @ r
+            q = Hbar @ s
+            a = np.real(np.vdot(s, s)) / np.real(np.vdot(q, q))
+            x, r = x + a * s, r - a * q
+            alphas.append(a)
+            betas.append(0.0)
+        return {"x": x, "alphas": alphas, "betas": betas, "breakdown": False}
+    assert orig is not no_beta
+    _plant(monkeypatch, "cgls", no_beta)
+    with pytest.raises(AssertionError):
+        test_cgls_detection_iterates_equal_cg(32, 8, 3)
