@@ -513,6 +513,12 @@ def run_ours(args):
             sweep[f"U16_K{kk}_{args.precision}"] = round(pair_ms(
                 cabi.params(B, Un, QAM, kk, R, N0, precision=prec), H, Y, T, n, xhat, mu, rho,
                 llr, st, q, qn, stp), 4)
+        sweep[f"U16_K3_{args.precision}_exact_tracker"] = round(pair_ms(
+            cabi.params(B, Un, QAM, K, R, N0, sinr_mode=1, precision=prec), H, Y, T, n, xhat,
+            mu, rho, llr, st, q, qn, stp), 4)
+        sweep["U16_K3_fp32_exact_tracker"] = round(pair_ms(
+            cabi.params(B, Un, QAM, K, R, N0, sinr_mode=1, precision=0), H, Y, T, n, xhat,
+            mu, rho, llr, st, q, qn, stp), 4)
         sweep["U16_K3_fp32_explicit"] = round(pair_ms(
             cabi.params(B, Un, QAM, K, R, N0, precision=0, amul_mode=1), H, Y, T, n, xhat, mu,
             rho, llr, st, q, qn, stp), 4)

@@ -97,6 +97,8 @@ int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void*
     const int UT = padded_users(p->U);
     if (!a.exact)
       err = launch_detect_warp(UT, el, x3, a, s);
+    else if (UT <= 16)
+      err = launch_detect_warp_exact(UT, el, x3, a, s);
     else
       err = launch_detect_tc(UT, el, x3, a, s, nullptr);
   }

@@ -173,6 +173,33 @@ __device__ __forceinline__ void ring_gram_prologue(unsigned char* ring, const fl
   for (int ks = 0; ks < RING_STAGES - 1; ++ks) ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, ks);
 }
 
+// Prefetch into L1 of the 8-antenna block ks of an instance's H with UT
+// users per row (U == UT: 8 rows of UT complex = UT / 2 lines of 128 bytes,
+// one per lane). Blocks past the end of H are skipped, so every address is
+// inside the instance. The register loads of the 16-byte paths run only one
+// block ahead; these keep several blocks of DRAM or L2 latency covered
+// without holding registers.
+template <int UT>
+__device__ __forceinline__ void prefetch_h_block(const float2* H, int B, int ks) {
+  constexpr int LINES = UT / 2;
+  const int lane = threadIdx.x & 31;
+  if (lane < LINES && 8 * ks < B) {
+    const int64_t byte = int64_t(ks) * (64 * UT) + int64_t(lane) * 128;
+    if (byte < int64_t(B) * UT * 8) {
+      const char* p = reinterpret_cast<const char*>(H) + byte;
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+    }
+  }
+}
+#ifndef CGM_PF_GRAM
+#define CGM_PF_GRAM 4  // blocks ahead in the Gram pass of the 16-byte path
+#endif
+#ifndef CGM_PF_Q
+#define CGM_PF_Q 3     // blocks ahead in the second pass over H (q = H v)
+#endif
+constexpr int PF_GRAM = CGM_PF_GRAM;
+constexpr int PF_Q = CGM_PF_Q;
+
 // q = H v n-tile nb (antennas 8 nb + g): the lane's H entries of users
 // 16 m + 4t..4t+3 for each m-tile m (two 16-byte loads each; 8 users: one
 // load of users 2t, 2t+1).
@@ -567,6 +594,101 @@ struct WarpCg {
     }
   }
 
+  // Eq. 10 for right-hand side `row` (alpha_k, beta_k in sAB, kdone
+  // iterations), then B = L_K G, C = L_K G L_K^H and, for the lane's matrix
+  // rows g + 8 hh (users at positions g + 8 hh; UT <= 16),
+  //   mu = Re B_ii,  nu^2 = Es sum_{j != i} |B_ij|^2 + N0 C_ii,  rho = mu^2 / nu^2.
+  // L_k is a polynomial in A with real coefficients, so it commutes with A
+  // and A (L_{k-1} - L_{k-2}) = (L_{k-1} - L_{k-2}) A: the 16 rows of the
+  // difference pass through matvec exactly like 16 right-hand sides, and
+  // every product of the recursion runs on the tensor cores. Rows and
+  // columns are in position order; p is overwritten.
+  __device__ __forceinline__ void exact_sinr(const uint2* frag, const float2* sAB, int row,
+                                             int kdone, float sigma, float N0, float Es,
+                                             float (&mu)[2], float (&rho)[2]) {
+    static_assert(UT <= 16, "the warp exact tracker holds one 16 x 16 tile");
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float2 L1[2][NB][2], L2[2][NB][2], L3[2][NB][2];
+    const float a1 = sAB[row].x;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const bool diag = (h == nt) && (g == 2 * t + c);
+          L1[h][nt][c] = make_float2(diag ? a1 : 0.f, 0.f);  // L_1 = alpha_1 I
+          L2[h][nt][c] = L3[h][nt][c] = make_float2(0.f, 0.f);
+        }
+    for (int k = 2; k <= kdone; ++k) {
+      const float2 abk = sAB[(k - 1) * 16 + row], ab1 = sAB[(k - 2) * 16 + row];
+      const float2 ab2 = k >= 3 ? sAB[(k - 3) * 16 + row] : make_float2(1.f, 0.f);
+      const float ak = abk.x;
+      const float c1 = ak * (1.f + ab1.y) / ab1.x;
+      const float c2 = ak * ab2.y / ab2.x;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+            p[h][nt][c] = make_float2(L1[h][nt][c].x - L2[h][nt][c].x,
+                                      L1[h][nt][c].y - L2[h][nt][c].y);
+      float Er[NB][4], Ei[NB][4];
+      matvec(frag, Er, Ei);  // (L_{k-1} - L_{k-2}) A
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const float2 d = p[h][nt][c];
+            const float2 l2 = L2[h][nt][c], l3 = L3[h][nt][c];
+            float2 ln;
+            ln.x = L1[h][nt][c].x + c1 * d.x - ak * Er[nt][2 * h + c] - c2 * (l2.x - l3.x);
+            ln.y = L1[h][nt][c].y + c1 * d.y - ak * Ei[nt][2 * h + c] - c2 * (l2.y - l3.y);
+            L3[h][nt][c] = l2;
+            L2[h][nt][c] = L1[h][nt][c];
+            L1[h][nt][c] = ln;
+          }
+    }
+    // B = L_K A - sigma L_K
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) p[h][nt][c] = L1[h][nt][c];
+    float Er[NB][4], Ei[NB][4];
+    matvec(frag, Er, Ei);
+    float dg[2] = {0.f, 0.f}, itf[2] = {0.f, 0.f}, cc[2] = {0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float2 l = L1[h][nt][c];
+          const float bx = fmaf(-sigma, l.x, Er[nt][2 * h + c]);
+          const float by = fmaf(-sigma, l.y, Ei[nt][2 * h + c]);
+          const bool diag = (h == nt) && (g == 2 * t + c);
+          if (diag)
+            dg[h] += bx;
+          else
+            itf[h] = fmaf(bx, bx, fmaf(by, by, itf[h]));
+          cc[h] = fmaf(bx, l.x, fmaf(by, l.y, cc[h]));  // Re(B_ij conj(L_ij))
+        }
+    quad_sum2(dg[0], dg[1]);
+    quad_sum2(itf[0], itf[1]);
+    quad_sum2(cc[0], cc[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      mu[h] = dg[h];
+      const float nu2 = fmaf(Es, itf[h], N0 * cc[h]);
+      rho[h] = nu2 > 0.f ? dg[h] * dg[h] / nu2 : 0.f;
+    }
+  }
+
   // Eq. 11 with A replaced by D (scalar per position) from the recorded
   // alpha_k, beta_k: l_1 = alpha_1, and for k >= 2
   //   l_k = l_{k-1} + (alpha_k (1 + beta_{k-1}) / alpha_{k-1} - alpha_k D)(l_{k-1} - l_{k-2})
@@ -791,9 +913,16 @@ __device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int 
   } else {
     constexpr bool V = LD == LD_VEC;
     float2 ha[MT][4], ya[4] = {}, hb[MT][4], yb[4] = {};
+    if constexpr (V)
+#pragma unroll
+      for (int d = 1; d <= PF_GRAM; ++d) prefetch_h_block<UT>(H, B, d);
     load_h_ks<UT, V>(H, B, U, 0, g, t, ha);
     if constexpr (MF) load_y_ks<V>(Y, B, R, 0, g, t, ya);
     for (int ks = 0; ks < KS; ks += 2) {  // ping-pong: loads run one k-step ahead
+      if constexpr (V) {
+        prefetch_h_block<UT>(H, B, ks + 1 + PF_GRAM);
+        prefetch_h_block<UT>(H, B, ks + 2 + PF_GRAM);
+      }
       if (ks + 1 < KS) {
         load_h_ks<UT, V>(H, B, U, ks + 1, g, t, hb);
         if constexpr (MF) load_y_ks<V>(Y, B, R, ks + 1, g, t, yb);
@@ -813,6 +942,7 @@ __device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int 
 // Solvers of the warp bodies: CG (Algorithm 1) or the Neumann series (Sec. III-F).
 constexpr int SOLVE_CG = 0;
 constexpr int SOLVE_NEUMANN = 1;
+constexpr int SOLVE_CG_EXACT = 2;  // CG with the exact tracker of Eq. 10 (UT <= 16)
 
 template <int UT, int EL, bool VEC, int SOLVER = SOLVE_CG>
 __device__ __forceinline__ int detect_warp_finish(const DetItem& it, uint2* frag, float2* sAB,
@@ -860,17 +990,62 @@ __device__ __forceinline__ int detect_warp_finish(const DetItem& it, uint2* frag
   for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
     for (int c = 0; c < 2; ++c) rho[nt][c] = Gd[nt][c] / it.N0;  // Eq. 13
+  // exact tracker: mu and rho of every right-hand side, gathered into the
+  // lanes that store its row (position P = 8 nt + 2 t + c of row r is held
+  // after exact_sinr by the lanes with g = 2 t + c, as their row half nt)
+  float emu[2][NB][2], erho[2][NB][2];
+  if constexpr (SOLVER == SOLVE_CG_EXACT) {
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+      for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) emu[hh][nt][c] = erho[hh][nt][c] = 0.f;
+    for (int r = 0; r < it.R; ++r) {
+      const bool upper = r >= 8;  // row half of r (register arrays take constant indices)
+      const int kdone = __shfl_sync(0xffffffffu, upper ? cg.kd[1] : cg.kd[0], 4 * (r & 7));
+      float m2[2] = {0.f, 0.f}, r2[2] = {0.f, 0.f};
+      if (kdone > 0) cg.exact_sinr(frag, sAB, r, kdone, it.sigma, it.N0, it.Es, m2, r2);
+#pragma unroll
+      for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int src = 4 * (2 * t + c) + t;
+          const float mv = __shfl_sync(0xffffffffu, m2[nt], src);
+          const float rv = __shfl_sync(0xffffffffu, r2[nt], src);
+          if (g == (r & 7)) {
+            if (upper) {
+              emu[1][nt][c] = mv;
+              erho[1][nt][c] = rv;
+            } else {
+              emu[0][nt][c] = mv;
+              erho[0][nt][c] = rv;
+            }
+          }
+        }
+    }
+  }
 #pragma unroll
   for (int hh = 0; hh < 2; ++hh) {
     const int r = g + 8 * hh;
     if (r >= it.R) continue;
     if (cg.broke[hh]) flags |= ST_BREAKDOWN;
     float mu[NB][2], l[NB][2];
-    cg.tracker_l(sAB, hh, l);
+    if constexpr (SOLVER == SOLVE_CG_EXACT) {
 #pragma unroll
-    for (int nt = 0; nt < NB; ++nt)
+      for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) mu[nt][c] = l[nt][c] * Gd[nt][c];  // Eq. 12
+        for (int c = 0; c < 2; ++c) {
+          mu[nt][c] = emu[hh][nt][c];
+          rho[nt][c] = erho[hh][nt][c];
+        }
+    } else {
+      cg.tracker_l(sAB, hh, l);
+#pragma unroll
+      for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) mu[nt][c] = l[nt][c] * Gd[nt][c];  // Eq. 12
+    }
     switch (it.q) {
       case 2: store_row_detect<UT, 2, VEC>(it, r, t, cg.v[hh], mu, rho, cq, &flags); break;
       case 4: store_row_detect<UT, 4, VEC>(it, r, t, cg.v[hh], mu, rho, cq, &flags); break;
@@ -1047,8 +1222,13 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
   constexpr int MT = WarpCfg<UT>::MT;
   const int NBQ = (it.B + 7) / 8;
   float4 fa[MT][2];
-  if constexpr (VEC) q_load<UT>(it.H, it.B, 0, g, t, fa);
+  if constexpr (VEC) {
+#pragma unroll
+    for (int d = 1; d <= PF_Q; ++d) prefetch_h_block<UT>(it.H, it.B, d);
+    q_load<UT>(it.H, it.B, 0, g, t, fa);
+  }
   for (int nb = 0; nb < NBQ; ++nb) {
+    if constexpr (VEC) prefetch_h_block<UT>(it.H, it.B, nb + 1 + PF_Q);
     const int b = 8 * nb + g;
     // lane's H entries at its k-positions: e[ks][j] = H(b, user(8 ks + 2 t + j))
     float2 e[NB][2];

@@ -56,6 +56,11 @@ cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const Ba
 // tracker only. Batch and serve forms as above (grid in CTAs of 4 warps).
 cudaError_t launch_detect_warp(int UT, int el, bool x3, const DetectArgs& a, cudaStream_t s);
 cudaError_t launch_precode_warp(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s);
+// CG-D with the exact tracker (Eq. 10) on the warp kernels, UT <= 16 (exact_warp.cu).
+cudaError_t launch_detect_warp_exact(int UT, int el, bool x3, const DetectArgs& a,
+                                     cudaStream_t s);
+cudaError_t launch_batch_warp_exact(int UT, int el, bool x3, const BatchArgs& b, int max_grid,
+                                    cudaStream_t s, bool launch, int* grid_out);
 // Neumann-series variants of the warp kernels (neumann.cu), Sec. III-F.
 cudaError_t launch_neumann_detect(int UT, int el, bool x3, const DetectArgs& a, cudaStream_t s);
 cudaError_t launch_neumann_precode(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s);

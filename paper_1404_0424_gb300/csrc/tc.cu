@@ -202,6 +202,10 @@ cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const Ba
     if (smem_out) *smem_out = 0;
     return launch_batch_warp(op, UT, el, x3, b, max_grid, s, launch, grid_out);
   }
+  if (op == 0 && UT <= 16) {  // exact tracker on the warp kernels, as the single calls
+    if (smem_out) *smem_out = 0;
+    return launch_batch_warp_exact(UT, el, x3, b, max_grid, s, launch, grid_out);
+  }
   switch (UT) {
     case 4:
     case 8: return batch_ut<8>(op, el, x3, full, b, max_grid, s, launch, smem_out, grid_out);

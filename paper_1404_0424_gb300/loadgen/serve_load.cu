@@ -19,7 +19,6 @@
 #include <cstring>
 #include <random>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "cgmimo.h"
@@ -263,8 +262,9 @@ int main(int argc, char** argv) {
       }
     }
     poll_ns += now_ns() - ts1;
-    if (served && next < reqs.size() && reqs[next].arrival_ns > now_ns() - t0 + 20000)
-      std::this_thread::sleep_for(std::chrono::microseconds(5));
+    // both modes poll without sleeping: a sleep of a few microseconds lasts
+    // the kernel's timer slack (tens of microseconds) and would delay the
+    // moment a completion is seen
   }
   const double elapsed = double(last_done - t0) * 1e-9;
   if (srv) cg_serve_destroy(srv);
