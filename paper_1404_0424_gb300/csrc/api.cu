@@ -149,10 +149,18 @@ int precode_device(const cg_params* p, int64_t n_inst, const void* H, const void
 // per device, used by one call at a time.
 // ---------------------------------------------------------------------------
 
+#ifndef CGM_HOST_STREAMS
+#define CGM_HOST_STREAMS 2
+#endif
+// Chunks in flight in the host-memory variants: chunk k runs on stream
+// k % kHostStreams in buffer set k % kHostStreams, so several host-to-device
+// and device-to-host copies proceed at once on the copy engines.
+constexpr int kHostStreams = CGM_HOST_STREAMS;
+
 struct HostWorkspace {
   void* d = nullptr;
   size_t bytes = 0;
-  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaStream_t st[kHostStreams] = {};
   cudaEvent_t ready = nullptr;
 };
 
@@ -168,7 +176,7 @@ int workspace_acquire(size_t need, HostWorkspace** out) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CG_ECUDA;
   HostWorkspace& w = g_ws[dev];
   if (w.st[0] == nullptr) {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < kHostStreams; ++i)
       if (cudaStreamCreateWithFlags(&w.st[i], cudaStreamNonBlocking) != cudaSuccess)
         return CG_ECUDA;
     if (cudaEventCreateWithFlags(&w.ready, cudaEventDisableTiming) != cudaSuccess)
@@ -188,13 +196,13 @@ int workspace_acquire(size_t need, HostWorkspace** out) {
 // Makes the workspace streams wait for earlier work on the caller's stream.
 int order_after(HostWorkspace* w, cudaStream_t user) {
   if (cudaEventRecord(w->ready, user) != cudaSuccess) return CG_ECUDA;
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < kHostStreams; ++i)
     if (cudaStreamWaitEvent(w->st[i], w->ready, 0) != cudaSuccess) return CG_ECUDA;
   return CG_OK;
 }
 
 int finish(HostWorkspace* w, int rc) {
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < kHostStreams; ++i)
     if (cudaStreamSynchronize(w->st[i]) != cudaSuccess && rc == CG_OK) rc = CG_ECUDA;
   return rc;
 }
@@ -330,15 +338,15 @@ int cg_detect_host(const cg_params* p, int64_t n_inst, const void* H, const void
   const size_t set = up256(oS + c * bS);
   std::lock_guard<std::mutex> lk(g_ws_mu);
   HostWorkspace* w = nullptr;
-  if ((rc = workspace_acquire(2 * set, &w)) != CG_OK) return rc;
+  if ((rc = workspace_acquire(kHostStreams * set, &w)) != CG_OK) return rc;
   if ((rc = order_after(w, static_cast<cudaStream_t>(stream))) != CG_OK) return rc;
   const char* hH = static_cast<const char*>(H);
   const char* hY = static_cast<const char*>(Y);
   int k = 0;
   for (int64_t off = 0; off < n_inst && rc == CG_OK; off += chunk, ++k) {
     const size_t nc = size_t(n_inst - off < chunk ? n_inst - off : chunk);
-    cudaStream_t s = w->st[k & 1];
-    char* base = static_cast<char*>(w->d) + (k & 1) * set;
+    cudaStream_t s = w->st[k % kHostStreams];
+    char* base = static_cast<char*>(w->d) + (k % kHostStreams) * set;
     if (h2d(base + oH, hH + off * bH, nc * bH, s) != cudaSuccess ||
         h2d(base + oY, hY + off * bY, nc * bY, s) != cudaSuccess) {
       rc = CG_ECUDA;
@@ -378,15 +386,15 @@ int cg_precode_host(const cg_params* p, int64_t n_inst, const void* H, const voi
   const size_t set = up256(oS + c * bS);
   std::lock_guard<std::mutex> lk(g_ws_mu);
   HostWorkspace* w = nullptr;
-  if ((rc = workspace_acquire(2 * set, &w)) != CG_OK) return rc;
+  if ((rc = workspace_acquire(kHostStreams * set, &w)) != CG_OK) return rc;
   if ((rc = order_after(w, static_cast<cudaStream_t>(stream))) != CG_OK) return rc;
   const char* hH = static_cast<const char*>(H);
   const char* hT = static_cast<const char*>(T);
   int k = 0;
   for (int64_t off = 0; off < n_inst && rc == CG_OK; off += chunk, ++k) {
     const size_t nc = size_t(n_inst - off < chunk ? n_inst - off : chunk);
-    cudaStream_t s = w->st[k & 1];
-    char* base = static_cast<char*>(w->d) + (k & 1) * set;
+    cudaStream_t s = w->st[k % kHostStreams];
+    char* base = static_cast<char*>(w->d) + (k % kHostStreams) * set;
     if (h2d(base + oH, hH + off * bH, nc * bH, s) != cudaSuccess ||
         h2d(base + oT, hT + off * bT, nc * bT, s) != cudaSuccess) {
       rc = CG_ECUDA;

@@ -28,7 +28,7 @@
 #include "cg_tc.cuh"
 
 #ifndef CGM_WARP_MINB
-#define CGM_WARP_MINB 4  // resident CTAs per SM the register allocation targets
+#define CGM_WARP_MINB 3  // resident CTAs per SM the register allocation targets
 #endif
 
 namespace cgm {
@@ -350,6 +350,10 @@ __device__ __forceinline__ void gram_ks(const float2 (&h)[WarpCfg<UT>::MT][4],
     const uint32_t s0l = swap_neg(b0.y), s1l = swap_neg(b1.y);
 #pragma unroll
     for (int m = 0; m < MT; ++m) {
+      // G is Hermitian: with two m-tiles (32 users) the block of rows 16..31 and
+      // columns 0..15 is the conjugate transpose of rows 0..15, columns 16..31,
+      // and WarpCg::setup_a takes it from there
+      if (MT == 2 && m == 1 && nt < 2) continue;
       const uint32_t ah[4] = {hs[m][0].x, hs[m][1].x, hs[m][2].x, hs[m][3].x};
       const uint32_t al[4] = {hs[m][0].y, hs[m][1].y, hs[m][2].y, hs[m][3].y};
       mma_split<EL, X3>(Gr[m][nt], ah, al, b0.x, b1.x, b0.y, b1.y);
@@ -401,8 +405,21 @@ struct WarpCg {
           // A[8 ks + 2 t + b][8 nt + g] = conj(G[8 nt + g][8 ks + 2 t + b]) (+ sigma)
           const int m = nt >> 1, d = 2 * (nt & 1) + b;
           const bool diag = (ks == nt) && (g == 2 * t + b);
-          const float re = Gr[m][ks][d] + (diag ? sigma : 0.f);
-          const float im = diag ? 0.f : -Gi[m][ks][d];
+          float re, im;
+          if (UT == 32 && m == 1 && ks < 2) {
+            // block not accumulated (gram_ks): A[i][j] = G[i][j] with i = 8 ks + 2 t + b
+            // in m-tile 0, held by lane 4 (2 t + b) + g / 2 at register 2 ks + g % 2
+            const int src = 4 * (2 * t + b) + (g >> 1);
+            const float r0 = __shfl_sync(0xffffffffu, Gr[0][nt][2 * ks], src);
+            const float r1 = __shfl_sync(0xffffffffu, Gr[0][nt][2 * ks + 1], src);
+            const float i0 = __shfl_sync(0xffffffffu, Gi[0][nt][2 * ks], src);
+            const float i1 = __shfl_sync(0xffffffffu, Gi[0][nt][2 * ks + 1], src);
+            re = (g & 1) ? r1 : r0;
+            im = (g & 1) ? i1 : i0;
+          } else {
+            re = Gr[m][ks][d] + (diag ? sigma : 0.f);
+            im = diag ? 0.f : -Gi[m][ks][d];
+          }
           frag[fidx(ks, nt, b, 0) * 32 + lane] = split_c<EL>(make_float2(re, im));
           if constexpr (STORE_IM)
             frag[fidx(ks, nt, b, 1) * 32 + lane] = split_c<EL>(make_float2(-im, re));
