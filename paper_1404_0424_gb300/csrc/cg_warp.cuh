@@ -28,7 +28,7 @@
 #include "cg_tc.cuh"
 
 #ifndef CGM_WARP_MINB
-#define CGM_WARP_MINB 3  // resident CTAs per SM the register allocation targets
+#define CGM_WARP_MINB 3  // resident CTAs per SM the register allocation targets at 16 users
 #endif
 
 namespace cgm {
@@ -48,7 +48,9 @@ struct WarpCfg {
   static constexpr int NFRAG = NB * NB * 2 * (STORE_IM ? 2 : 1);  // (ks, nt, b0/b1[, re/im])
   static constexpr int WARPS = 4;                // warps per CTA (independent)
   static constexpr int NTHR = 32 * WARPS;
-  static constexpr int MINB = UT == 32 ? 2 : CGM_WARP_MINB;  // resident CTAs per SM targeted
+  // resident CTAs per SM targeted: 8 users fit 4 CTAs in 128 registers; 16
+  // users run faster at 3 CTAs without spills than at 4 with them
+  static constexpr int MINB = UT == 32 ? 2 : UT == 16 ? CGM_WARP_MINB : 4;
   // per warp: a ring of RING_STAGES load stages (PLANES planes of 16 bytes
   // per lane each), the CG B fragments (one uint2 per lane and fragment), and
   // alpha_k, beta_k of the 16 right-hand-side rows for the tracker (K <= UT)
