@@ -276,16 +276,19 @@ typedef struct cg_req_stats {
 typedef struct cg_server cg_server;
 
 /* Creates a server on the current device and starts nothing yet. Requests
- * fall into classes by operation and padded user count (8, 16, 32), plus one
- * for exact-tracker detection, each published in order through its own ring
- * in pinned, mapped host memory. One persistent kernel serves the six
- * approximate-tracker classes: each of its warps takes instances of the
- * oldest request of its home class while there are any, and otherwise of
- * another class that has work, so a request alone on the device is spread
- * over every SM, and requests that arrive while others run are admitted as
- * warps free up. A second kernel serves the exact class. Each kernel
- * launches on the first request that needs it, on its own stream, and exits
- * after idle_timeout_ms without work. Every device wait is bounded. */
+ * fall into classes by operation and padded user count (8, 16, 32), and for
+ * exact-tracker detection by padded user count too; each class publishes in
+ * order through its own ring in pinned, mapped host memory. One persistent
+ * kernel serves every class up to 16 users with the exact tracker and every
+ * approximate-tracker class: each of its warps takes instances of the oldest
+ * request of its home class while there are any, and otherwise of another
+ * class that has work, so a request alone on the device is spread over every
+ * SM, and requests that arrive while others run are admitted as warps free
+ * up. A second kernel serves exact-tracker detection with 32 padded users.
+ * Each kernel launches on the first request that needs it, on its own
+ * stream, and exits after idle_timeout_ms without work. A served request
+ * gives the same bits as the single call of the same precision. Every device
+ * wait is bounded. */
 int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out);
 
 /* Non-blocking submit of one request (a cg_desc with 1 <= n_inst < 2^24

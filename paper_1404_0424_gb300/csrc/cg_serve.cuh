@@ -65,8 +65,9 @@ struct ServeCompletion {
 // class_tail index of the total over all classes (host-written); the same
 // index of the device head array holds the device's copy of that total, and
 // kServeStop a device copy of the stop flag.
-constexpr int kServeTotal = 7;
-constexpr int kServeStop = 8;
+constexpr int kServeMaxClasses = 14;  // classes 0..13 may be used
+constexpr int kServeTotal = 15;
+constexpr int kServeStop = 14;
 constexpr int kServeHeadWords = 16;
 
 // Control block in mapped host memory: the stop flag and the class tails
@@ -76,11 +77,11 @@ constexpr int kServeHeadWords = 16;
 // without a CUDA call.
 
 struct ServeCtrl {
-  unsigned long long class_tail[8];  // requests published per class; [7]: all classes
+  unsigned long long class_tail[16];  // requests published per class; [15]: all classes
   int stop;
   int pad;
-  int live[8];
-  unsigned long long exited_gen[8];
+  int live[16];
+  unsigned long long exited_gen[16];
 };
 
 // Threads of a serving CTA of the warp-per-instance kernels (8 warps: one
@@ -400,12 +401,13 @@ __global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
 
 
 // ---------------------------------------------------------------------------
-// Serving: one kernel for the six (operation, padded users) classes of the
-// approximate tracker
+// Serving: one kernel for the warp-per-instance classes
 // ---------------------------------------------------------------------------
 
-// Classes 0-2 detect with 8, 16, 32 padded users, 3-5 precode.
-constexpr int kWarpClasses = 6;
+// Classes 0-2 detect with 8, 16, 32 padded users, 3-5 precode, 6-7 detect with
+// the exact tracker (Eq. 10) with 8 and 16 padded users.
+constexpr int kWarpClasses = 8;
+static_assert(kWarpClasses < kServeMaxClasses, "a class index past the warp classes remains");
 // Every warp owns a slice large enough for any class, since the warps of one
 // CTA may serve different classes at the same time.
 constexpr uint32_t kServeSlice = WarpCfg<32>::WARP_BYTES;
@@ -432,6 +434,10 @@ template <int UT, int EL, bool X3>
 __device__ __noinline__ void serve_precode(const ServeArgs& s, unsigned char* mine) {
   precode_warp_body<UT, EL, X3>(s, mine);
 }
+template <int UT, int EL, bool X3>
+__device__ __noinline__ void serve_detect_exact(const ServeArgs& s, unsigned char* mine) {
+  detect_warp_body<UT, EL, X3, ServeArgs, SOLVE_CG_EXACT>(s, mine);
+}
 
 template <int EL, bool X3>
 __device__ __forceinline__ void serve_class(int c, const ServeWarpArgs& p, unsigned char* mine) {
@@ -441,7 +447,9 @@ __device__ __forceinline__ void serve_class(int c, const ServeWarpArgs& p, unsig
     case 2: serve_detect<32, EL, X3>(p.c[2], mine); break;
     case 3: serve_precode<8, EL, X3>(p.c[3], mine); break;
     case 4: serve_precode<16, EL, X3>(p.c[4], mine); break;
-    default: serve_precode<32, EL, X3>(p.c[5], mine); break;
+    case 5: serve_precode<32, EL, X3>(p.c[5], mine); break;
+    case 6: serve_detect_exact<8, EL, X3>(p.c[6], mine); break;
+    default: serve_detect_exact<16, EL, X3>(p.c[7], mine); break;
   }
 }
 

@@ -25,10 +25,12 @@ using namespace cgm;
 
 namespace {
 
-// (detect, precode) x (UT 8, 16, 32) on the warp-per-instance serving kernel,
-// and exact-tracker detection on the CTA kernel (32 padded users)
-constexpr int kClasses = 7;
-constexpr int kExactClass = 6;
+// (detect, precode) x (UT 8, 16, 32) and exact-tracker detection with 8 or 16
+// padded users on the warp-per-instance serving kernel (classes 0-7), and
+// exact-tracker detection with 32 padded users on the CTA kernel (class 8)
+constexpr int kClasses = 9;
+constexpr int kExactClass = 8;
+static_assert(kClasses <= kServeMaxClasses, "class count of the control block");
 constexpr int kRingPerSlot = 4;   // class ring positions per slot (ring = 4 x capacity)
 // Serving kernels: 0 serves classes 0-5, 1 the exact class. A kernel's
 // liveness counters in the control block are those of its ServeArgs::cls.
@@ -43,12 +45,14 @@ int64_t mono_ns() {
 }
 
 // Class of a request: (operation, padded users 8 / 16 / 32), one warp per
-// instance; detection with the exact tracker has a class of its own whose
-// CTA kernel has the shared memory for the U x U recursion of Eq. 10.
+// instance; detection with the exact tracker (Eq. 10) has classes 6 and 7 on
+// the warp kernel up to 16 users (as single calls and plans) and class 8 on
+// the CTA kernel, whose shared memory holds the 32 x 32 recursion.
 int class_of(const cg_desc& d, int* UT) {
   const int pu = padded_users(d.U);
   *UT = pu < 8 ? 8 : pu;
   if (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT) {
+    if (*UT <= 16) return *UT == 8 ? 6 : 7;
     *UT = 32;
     return kExactClass;
   }

@@ -139,6 +139,43 @@ def test_same_result_alone_and_in_the_mix(cabi):
             assert torch.equal(m[k], ref[k]), f"served {k} differs from the single call"
 
 
+def test_exact_tracker_requests(cabi):
+    # exact-tracker detection (Eq. 10): up to 16 users on the warp serving kernel,
+    # bitwise equal to the single call; at 32 users on the CTA serving kernel,
+    # checked against the FP64 oracle
+    import oracle
+    from tests.parity import check_detect, to_np
+    dev = torch.device("cuda:0")
+    reqs = []
+    for k, (B, U) in enumerate([(64, 8), (128, 16), (100, 12), (128, 32)]):
+        R, q, K = 5, 4, min(U, 4)
+        d = wl.uplink_torch(B, U, q, n=40, R=R, snr_db=8.0, seed=700 + k, device=dev)
+        reqs.append(dict(op=0, B=B, U=U, R=R, q=q, K=K, n=40, N0=d["N0"], H=d["H"], inp=d["Y"]))
+    rc, srv = cabi.cg_serve_create(capacity=16, precision=4, idle_timeout_ms=300)
+    assert rc == 0, cabi.cg_strerror(rc)
+    outs = [fresh_outputs(r, dev) for r in reqs]
+    try:
+        tickets = []
+        for r, o in zip(reqs, outs):
+            dsc = cabi.desc(0, r["B"], r["U"], r["R"], r["K"], r["N0"], r["H"], r["inp"],
+                            o["xhat"], qam_bits=r["q"], sinr_mode=1, mu=o["mu"], rho=o["rho"],
+                            aux=o["llr"], status=o["status"])
+            tickets.append(submit(cabi, srv, dsc))
+        wait_done(cabi, srv, tickets)
+    finally:
+        assert cabi.cg_serve_destroy(srv) == 0
+    for r, o in zip(reqs, outs):
+        if r["U"] <= 16:
+            ref = cabi.detect(r["H"], r["inp"], r["N0"], r["K"], r["q"], sinr_mode=1, precision=4)
+            torch.cuda.synchronize()
+            for k in o:
+                assert torch.equal(o[k], ref[k]), f"served exact {k} differs at U={r['U']}"
+        else:
+            ref = oracle.cg_detect(r["H"].cpu().numpy(), r["inp"].cpu().numpy(), r["N0"], 1.0,
+                                   r["K"], r["q"], "exact")
+            check_detect({k: to_np(v) for k, v in o.items()}, ref)
+
+
 def test_admission_by_slots_and_budget(cabi):
     dev = torch.device("cuda:0")
     r = make_requests(dev, n_req=1, seed=9)[0]
