@@ -613,6 +613,37 @@ def run_ours(args):
             ne * (R * B * 8 + R * 4 + 4)
         e2e = {"value": 2 * ne * R / dt, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "instances_per_step": ne}
+        # the host link itself: one large pinned copy each way, then both at once
+        # on two streams; the step's bytes over its time set against them
+        big = 512 << 20
+        hsrc = torch.empty(big, dtype=torch.uint8).pin_memory()
+        hdst = torch.empty(big, dtype=torch.uint8).pin_memory()
+        dbuf = torch.empty(big, dtype=torch.uint8, device=dev)
+        dbuf2 = torch.empty(big, dtype=torch.uint8, device=dev)
+        s2 = torch.cuda.Stream(dev)
+
+        def copy_gbs(fn, nbytes, reps=5):
+            fn()
+            torch.cuda.synchronize()
+            t0c = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize()
+            return nbytes * reps / (time.perf_counter() - t0c) / 1e9
+
+        def both():
+            dbuf.copy_(hsrc, non_blocking=True)
+            with torch.cuda.stream(s2):
+                hdst.copy_(dbuf2, non_blocking=True)
+        h2d_gbs = copy_gbs(lambda: dbuf.copy_(hsrc, non_blocking=True), big)
+        d2h_gbs = copy_gbs(lambda: hdst.copy_(dbuf, non_blocking=True), big)
+        both_gbs = copy_gbs(both, 2 * big)
+        e2e["host_link"] = {"h2d_gbs": round(h2d_gbs, 1), "d2h_gbs": round(d2h_gbs, 1),
+                            "both_directions_gbs": round(both_gbs, 1),
+                            "step_gbs": round((h2d + d2h) / dt / 1e9, 1),
+                            "what": "pinned copies of 512 MiB; step_gbs = the e2e step's "
+                                    "host<->device bytes over its time"}
+        del hsrc, hdst, dbuf, dbuf2
         cabi.cg_release_workspace()
 
     peaks, peak_kind = measured_peaks()
