@@ -65,6 +65,64 @@ PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3, "fp16x3": 4}
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (read-only queries)
+    every millisecond on a thread, so a timed region of a few milliseconds
+    still gets samples under load."""
+    # NVML clock-event reason bits (nvmlClocksEventReason*)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index: int):
+        import ctypes
+        import threading
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)):
+            raise OSError("no NVML handle")
+        self.get_reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples = []
+        self.stop_flag = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        ct = self.ct
+        clk, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_flag.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(clk)) == 0 and \
+                    self.get_reasons(self.h, ct.byref(rs)) == 0:
+                self.samples.append((clk.value, rs.value))
+            time.sleep(0.001)
+
+    def start(self):
+        self.thread.start()
+
+    def stop(self) -> dict:
+        self.stop_flag.set()
+        self.thread.join(timeout=5)
+        mx = self.ct.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, self.ct.byref(mx))
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": mx.value, "reasons": ["no samples"]}
+        reasons = sorted({nm for _, r in self.samples for bit, nm in self.REASONS.items()
+                          if r & bit})
+        return {"sm_mhz": statistics.median(c for c, _ in self.samples),
+                "sm_max_mhz": mx.value, "reasons": reasons, "samples": len(self.samples),
+                "source": "nvml, 1 ms"}
+
+
+def clock_sampler(index: int):
+    """NVML sampler when the library loads, else nvidia-smi at 200 ms."""
+    try:
+        return NvmlClockSampler(index)
+    except (OSError, AttributeError):
+        return ClockSampler(index)
+
+
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -413,7 +471,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     assert int(st.abs().sum()) == 0 and int(stp.abs().sum()) == 0
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(local)
     clocks.start()
     if dist:
         dist.barrier()
