@@ -411,6 +411,24 @@ def test_exact_convergence_stops_the_iteration():
     np.testing.assert_allclose(o["mu"], [0.5, 2.0])   # l_1 = alpha_1 = 1/2, mu = l G_ii
 
 
+def test_exact_tracker_L_is_a_real_polynomial_in_A():
+    # every L_k of Eq. 10 is a real-coefficient polynomial in A, hence Hermitian and
+    # commuting with A (the property the tensor-core exact tracker relies on: it forms
+    # A (L_{k-1} - L_{k-2}) as (L_{k-1} - L_{k-2}) A); and L_k b reproduces the iterate
+    H = crandn(RNG, 40, 6)
+    y = crandn(RNG, 40)
+    A = orc.regularised_gram(H, 0.5, 1.0)
+    b = orc.matched_filter(H, y)
+    cg = orc.conjugate_gradient(A, b, 5)
+    Ls = orc.exact_tracker_L(cg["alphas"], cg["betas"], A)
+    assert len(Ls) == 5
+    for k, L in enumerate(Ls, start=1):
+        scale = np.abs(L).max()
+        np.testing.assert_allclose(L @ A, A @ L, atol=1e-12 * scale * np.abs(A).max())
+        np.testing.assert_allclose(L, L.conj().T, atol=1e-13 * scale)
+        np.testing.assert_allclose(L @ b, cg["iterates"][k], rtol=1e-10)
+
+
 # ---------------------------------------------------------------------------
 # Truncated Neumann series (Sec. III-F)
 # ---------------------------------------------------------------------------
