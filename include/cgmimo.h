@@ -6,7 +6,9 @@
  * Gradient-based Soft-Output Detection and Precoding in Massive MIMO Systems"
  * (arXiv 1404.0424), run in bulk: one CG solve per (instance, right-hand
  * side). An instance is one subcarrier: a channel H shared by R right-hand
- * sides (OFDM symbols).
+ * sides (OFDM symbols). The paper's comparison methods are offered beside
+ * it: CG least squares (Sec. III-E, amul_mode CG_AMUL_CGLS) and the
+ * truncated Neumann series (Sec. III-F, cg_neumann_detect/cg_neumann_precode).
  *
  * Data layout (row-major, no padding, little-endian):
  *   complex values are complex64: interleaved (re, im) float32 pairs;
@@ -56,7 +58,8 @@ extern "C" {
 #define CG_EAGAIN (-4)     /* resource temporarily full (serving queue) */
 #define CG_ETIMEDOUT (-5)  /* a bounded wait expired */
 #define CG_ENOTSUP (-6)    /* valid but unsupported combination of modes */
-#define CG_ETOOBIG (-7)    /* request exceeds a fixed capacity (cg_batch_run_static) */
+#define CG_ETOOBIG (-7)    /* request exceeds a fixed capacity (cg_batch_run_static,
+                              or a served request larger than the HBM budget) */
 
 /* Per-instance status bits. */
 #define CG_STATUS_BREAKDOWN 1  /* CG stopped before K: ||r_{k-1}||^2 or Re(p^H A p) not > 0 */
@@ -91,7 +94,9 @@ extern "C" {
  * variants; the batched and serving entry points always form the Gram. */
 #define CG_AMUL_CGLS 3
 
-/* Arithmetic of the Gram H^H H and matched filter H^H y (CG itself is FP32). */
+/* Arithmetic of the Gram H^H H and matched filter H^H y; on the tensor-core
+ * paths the products A p and q = H v use the same operands (the CG vectors,
+ * step sizes and sums are FP32 in every mode). */
 #define CG_PREC_FP32 0
 #define CG_PREC_BF16 1    /* one BF16 tensor-core pass, FP32 accumulate */
 #define CG_PREC_FP16 2    /* one FP16 tensor-core pass, FP32 accumulate */
