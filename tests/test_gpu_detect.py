@@ -200,3 +200,27 @@ def test_implicit_product_with_exact_tracker_is_not_supported(cabi):
     d = wl.uplink(32, 4, 4, n=2, R=1, snr_db=10.0, seed=72)
     with pytest.raises(cabi.CgError):
         run(cabi, d, 2, tracker="exact", amul_mode=2)
+
+
+@pytest.mark.parametrize("precision", [0, 4])
+@pytest.mark.parametrize("tracker", ["approx", "exact"])
+def test_every_maximum_at_once(cabi, precision, tracker):
+    # B = CG_B_MAX, U = CG_U_MAX, R = CG_R_MAX, K = U, 256-QAM. At K = U the FP32
+    # iteration may meet ||r||^2 = 0 or p^H A p <= 0 after it has converged to FP32
+    # resolution and stop there with CG_STATUS_BREAKDOWN, where FP64 goes on: outputs
+    # must still match, and an extra BREAKDOWN flag is accepted only for an instance
+    # whose FP64 residual was already below 1e-5 (relative) one iteration before K
+    K = 32
+    d = wl.uplink(256, 32, 8, n=2, R=16, snr_db=12.0, seed=4242)
+    g = run(cabi, d, K, tracker, precision=precision)
+    r = ref(d, K, tracker)
+    check_detect(g, r, check_status=False)
+    for i in range(2):
+        if g["status"][i] == r["status"][i]:
+            continue
+        assert g["status"][i] == r["status"][i] | oracle.STATUS_BREAKDOWN, (g["status"], r["status"])
+        A = oracle.regularised_gram(d["H"][i], d["N0"], d["Es"])
+        for rr in range(16):
+            b = oracle.matched_filter(d["H"][i], d["Y"][i, rr])
+            x = oracle.conjugate_gradient(A, b, K - 1)["v"]
+            assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) < 1e-5, (i, rr)

@@ -125,3 +125,10 @@ def test_implicit_product_matches_oracle(cabi, B, U, R, K, normalize):
     torch.cuda.synchronize()
     check_precode({k: to_np(v) for k, v in out.items()},
                   oracle.cg_precode(d["H"], d["T"], d["N0"], d["Es"], K), normalize=normalize)
+
+
+@pytest.mark.parametrize("normalize", [False, True])
+def test_every_maximum_at_once(cabi, normalize):
+    # B = CG_B_MAX, U = CG_U_MAX, R = CG_R_MAX, K = U
+    d = wl.downlink(256, 32, 8, n=2, R=16, snr_db=12.0, seed=4343)
+    check_precode(run(cabi, d, 32, normalize), ref(d, 32), normalize)
