@@ -118,3 +118,27 @@ def test_serve_rejects_invalid_configuration_on_the_host(lib):
     assert cabi.cg_serve_submit(None, good)[0] == cabi.CG_EINVAL
     assert cabi.cg_serve_poll(None, 0)[0] == cabi.CG_EINVAL
     assert lib.cg_serve_destroy(None) == cabi.CG_EINVAL
+
+
+def test_cgls_and_neumann_reject_on_the_host(lib):
+    # CGLS needs no Gram, so it does not combine with the exact tracker
+    p = cabi.params(32, 4, 4, 3, 1, 0.4, sinr_mode=1, amul_mode=cabi.CG_AMUL_CGLS)
+    assert cabi.cg_detect(p, 1, 16, 16) == cabi.CG_ENOTSUP
+    p = cabi.params(32, 4, 4, 3, 1, 0.4, amul_mode=cabi.CG_AMUL_CGLS + 1)
+    assert cabi.cg_detect(p, 1, 16, 16) == cabi.CG_EINVAL
+    # Neumann series: 1 <= K <= CG_NEUMANN_K_MAX terms, a tensor-core precision,
+    # x_hat (detection) or q (precoding) required
+    for K, prec, want in [(0, 4, cabi.CG_EINVAL), (cabi.CG_NEUMANN_K_MAX + 1, 4, cabi.CG_EINVAL),
+                          (3, cabi.CG_PREC_FP32, cabi.CG_ENOTSUP), (3, 9, cabi.CG_EINVAL)]:
+        p = cabi.params(32, 4, 4, K, 1, 0.4, precision=prec)
+        assert cabi.cg_neumann_detect(p, 1, 16, 16, 16) == want, (K, prec)
+        assert cabi.cg_neumann_precode(p, 1, 16, 16, 16) == want, (K, prec)
+    p = cabi.params(32, 4, 4, 3, 1, 0.4, precision=4)
+    assert cabi.cg_neumann_detect(p, 1, 16, 16, None) == cabi.CG_EINVAL
+    assert cabi.cg_neumann_detect(p, 1, 16, 12, 16) == cabi.CG_EINVAL   # Y not 8-byte aligned
+    assert cabi.cg_neumann_detect(p, -1, 16, 16, 16) == cabi.CG_EINVAL
+    assert cabi.cg_neumann_precode(p, 1, 16, 16, None) == cabi.CG_EINVAL
+    assert cabi.cg_neumann_precode(p, 1, None, 16, 16) == cabi.CG_EINVAL
+    assert lib.cg_neumann_detect(None, 1, None, None, None, None, None) == cabi.CG_EINVAL
+    assert lib.cg_neumann_precode(None, 1, None, None, None, None, 0, None, None) == \
+        cabi.CG_EINVAL
