@@ -164,3 +164,24 @@ def test_precode_one_pass_error_is_bounded(cabi, mode):
     err = (np.linalg.norm(g["q"] - r["q"], axis=-1) / np.linalg.norm(r["q"], axis=-1)).max()
     print(f"{mode}: max relative q error {err:.3e}")
     assert err <= bound
+
+
+def test_bench_launch_38400_instances_sampled(cabi):
+    # the benchmark's own launch: 32 slots of 1200 subcarriers x 14 symbols (38,400
+    # instances), 128 x 16, 64-QAM, K = 3, FP16 hi+lo, detection and precoding in one
+    # call each, checked on sampled instances against the FP64 oracle
+    dev = torch.device("cuda:0")
+    d = wl.uplink_torch(128, 16, 6, n=38400, R=14, snr_db=10.0, seed=1000, device=dev)
+    T = d["x"].contiguous()
+    out = cabi.detect(d["H"], d["Y"], d["N0"], 3, 6, precision=4)
+    pre = cabi.precode(d["H"], T, d["N0"], 3, precision=4)
+    torch.cuda.synchronize()
+    assert int(out["status"].abs().sum()) == 0 and int(pre["status"].abs().sum()) == 0
+    idx = np.sort(np.random.default_rng(38400).choice(38400, 8, replace=False))
+    H = d["H"][idx].cpu().numpy()
+    check_detect({k: to_np(v[idx]) for k, v in out.items()},
+                 oracle.cg_detect(H, d["Y"][idx].cpu().numpy(), d["N0"], 1.0, 3, 6))
+    check_precode({k: to_np(v[idx]) for k, v in pre.items()},
+                  oracle.cg_precode(H, T[idx].cpu().numpy(), d["N0"], 1.0, 3))
+    del d, out, pre, T
+    torch.cuda.empty_cache()
