@@ -379,6 +379,21 @@ def run_large(cabi, torch, dev, precision):
     e[2].record(stream)
     torch.cuda.synchronize()
     dms, pms = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+    # the exact tracker (Eq. 10) on the tensor cores against the FP32
+    # CUDA-core kernel, the latter on a quarter of the batch (x4 reported)
+    pe = cabi.params(Bl, Ul, ql, Kl, Rl, N0, sinr_mode=1, precision=PRECISIONS[precision])
+    pf = cabi.params(Bl, Ul, ql, Kl, Rl, N0, sinr_mode=1, precision=0)
+    nq = nl // 4
+    cabi.cg_detect(pe, nl, H, Y, xhat, mu, rho, llr, st, stream)
+    cabi.cg_detect(pf, nq, H, Y, xhat, mu, rho, llr, st, stream)
+    e[0].record(stream)
+    for _ in range(2):
+        cabi.cg_detect(pe, nl, H, Y, xhat, mu, rho, llr, st, stream)
+    e[1].record(stream)
+    cabi.cg_detect(pf, nq, H, Y, xhat, mu, rho, llr, st, stream)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    exact_ms, exact_fp32_ms = e[0].elapsed_time(e[1]) / 2, e[1].elapsed_time(e[2]) * 4
     peaks, kind = measured_peaks()
     db = detect_bytes_per_instance(Bl, Ul, Rl, ql) * nl
     pb = precode_bytes_per_instance(Bl, Ul, Rl) * nl
@@ -389,7 +404,9 @@ def run_large(cabi, torch, dev, precision):
            "detect_gbs": round(db / dms / 1e6, 1), "precode_gbs": round(pb / pms / 1e6, 1),
            "detect_frac_hbm": round(db / dms / 1e6 / peaks["hbm_gbs"], 4),
            "precode_frac_hbm": round(pb / pms / 1e6 / peaks["hbm_gbs"], 4),
-           "peak_kind": kind, "status_ok": ok}
+           "peak_kind": kind, "status_ok": ok,
+           "exact_tracker_detect_ms": round(exact_ms, 4),
+           "exact_tracker_fp32_detect_ms": round(exact_fp32_ms, 3)}
     del H, Y, T, xhat, mu, rho, llr, st, q, qn, stp
     torch.cuda.empty_cache()
     return out

@@ -353,14 +353,19 @@ int cg_serve_destroy(cg_server* s);
  *
  * Limits: more than CG_STATIC_MAX_PROBLEMS problems or more than
  * CG_STATIC_MAX_INSTANCES instances in total returns CG_ETOOBIG with no
- * work enqueued; invalid descriptors return CG_EINVAL.
+ * work enqueued; invalid descriptors return CG_EINVAL, also with no work
+ * enqueued (every bin's launch shape is checked before the first copy).
+ * CG_ECUDA from a copy or a launch may leave the work of earlier bins
+ * enqueued. Descriptors with n_inst = 0 are validated and then skipped.
+ * Exact-tracker detection runs in bins of its own, as in cg_plan_create.
  *
- * The first call on a device looks up the device address of the static
- * array on that device (make the device current first); make that first
- * call before any stream capture. Every call reuses the same array, which
- * keeps the previous call's contents; the call resets the parts that must
- * start at zero. Calls whose work overlaps on the GPU (different streams,
- * or other threads) race on the array: order them on one stream. */
+ * Each call looks up the device address of the static array on the
+ * current device (make the device current first); the first call on a
+ * device may load the library's device code, so make it before any stream
+ * capture. Every call reuses the same array, which keeps the previous
+ * call's contents; the call resets the parts that must start at zero.
+ * Calls whose work overlaps on the GPU (different streams, or other
+ * threads) race on the array: order them on one stream. */
 int cg_batch_run_static(const cg_desc* descs, int64_t n, int32_t precision, void* stream);
 
 /* Frees the workspace of the *_host calls on the current device. */

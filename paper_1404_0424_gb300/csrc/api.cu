@@ -95,12 +95,8 @@ int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void*
     bool x3;
     tc_mode(p->precision, &el, &x3);
     const int UT = padded_users(p->U);
-    if (!a.exact)
-      err = launch_detect_warp(UT, el, x3, a, s);
-    else if (UT <= 16)
-      err = launch_detect_warp_exact(UT, el, x3, a, s);
-    else
-      err = launch_detect_tc(UT, el, x3, a, s, nullptr);
+    err = a.exact ? launch_detect_warp_exact(UT, el, x3, a, s)
+                  : launch_detect_warp(UT, el, x3, a, s);
   }
   if (err == cudaErrorInvalidValue) return CG_EINVAL;
   return err == cudaSuccess ? CG_OK : CG_ECUDA;
@@ -135,10 +131,7 @@ int precode_device(const cg_params* p, int64_t n_inst, const void* H, const void
     bool x3;
     tc_mode(p->precision, &el, &x3);
     const int UT = padded_users(p->U);
-    if (UT <= 32)
-      err = launch_precode_warp(UT, el, x3, a, s);
-    else
-      err = launch_precode_tc(UT, el, x3, a, s, nullptr);
+    err = launch_precode_warp(UT, el, x3, a, s);
   }
   if (err == cudaErrorInvalidValue) return CG_EINVAL;
   return err == cudaSuccess ? CG_OK : CG_ECUDA;

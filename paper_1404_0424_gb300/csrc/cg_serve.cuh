@@ -1,10 +1,9 @@
 // Serving: requests published by the host through mapped host memory and
 // claimed instance by instance by persistent kernels (cg_serve_*).
 //
-// Work units take their instances through the same bodies as the single
-// calls and the batched plans: the CTA tensor-core bodies (exact tracker)
-// and the warp-per-instance bodies (approximate tracker), with ServeArgs as
-// their work source.
+// Work units take their instances through the same warp-per-instance bodies
+// as the single calls and the batched plans, with ServeArgs as their work
+// source.
 #pragma once
 
 #include "cg_warp.cuh"
@@ -272,12 +271,6 @@ __device__ __forceinline__ int64_t serve_claim_wait(const ServeArgs& s) {
   }
 }
 
-// Thread 0 claims for its CTA (serve_claim_wait) into shared memory.
-__device__ __forceinline__ void claim_next(const ServeArgs& s, int64_t* slot) {
-  if (threadIdx.x != 0) return;
-  *slot = serve_claim_wait(s);
-}
-
 // Non-blocking claim by one thread: -2 when no work is available yet (try
 // again later; the stop flag is seen by the waiting claim that follows).
 __device__ __forceinline__ int64_t serve_claim_try(const ServeArgs& s) {
@@ -287,11 +280,6 @@ __device__ __forceinline__ int64_t serve_claim_try(const ServeArgs& s) {
   }
 }
 
-// Thread 0 of a CTA, non-blocking (serve_claim_try) into shared memory.
-__device__ __forceinline__ void claim_try(const ServeArgs& s, int64_t* slot) {
-  if (threadIdx.x != 0) return;
-  *slot = serve_claim_try(s);
-}
 
 // The descriptor of a work unit's request, from its device copy.
 __device__ __forceinline__ cg_desc serve_desc(const ServeArgs& s, int64_t w) {
@@ -381,32 +369,13 @@ __device__ __forceinline__ int64_t warp_try(const ServeArgs& s) {
   return __shfl_sync(0xffffffffu, w, 0);
 }
 
-// CTA serving kernels (exact-tracker detection): every CTA claims
-// instances of the oldest request of its class until stopped or idle.
-template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
-    detect_tc_serve_kernel(const ServeArgs s) {
-  if (threadIdx.x == 0) serve_unit_enter(s);
-  detect_tc_body<UT, EL, X3, false>(s, s.PB, UT, s.PR, s.PEX);
-  if (threadIdx.x == 0) serve_unit_exit(s);
-}
-
-template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(TcCfg<UT>::NTHR, UT == 32 ? 1 : 4)
-    precode_tc_serve_kernel(const ServeArgs s) {
-  if (threadIdx.x == 0) serve_unit_enter(s);
-  precode_tc_body<UT, EL, X3, false>(s, s.PB, UT, s.PR);
-  if (threadIdx.x == 0) serve_unit_exit(s);
-}
-
-
 // ---------------------------------------------------------------------------
 // Serving: one kernel for the warp-per-instance classes
 // ---------------------------------------------------------------------------
 
-// Classes 0-2 detect with 8, 16, 32 padded users, 3-5 precode, 6-7 detect with
-// the exact tracker (Eq. 10) with 8 and 16 padded users.
-constexpr int kWarpClasses = 8;
+// Classes 0-2 detect with 8, 16, 32 padded users, 3-5 precode, 6-8 detect with
+// the exact tracker (Eq. 10) with 8, 16 and 32 padded users.
+constexpr int kWarpClasses = 9;
 static_assert(kWarpClasses < kServeMaxClasses, "a class index past the warp classes remains");
 // Every warp owns a slice large enough for any class, since the warps of one
 // CTA may serve different classes at the same time.
@@ -449,7 +418,8 @@ __device__ __forceinline__ void serve_class(int c, const ServeWarpArgs& p, unsig
     case 4: serve_precode<16, EL, X3>(p.c[4], mine); break;
     case 5: serve_precode<32, EL, X3>(p.c[5], mine); break;
     case 6: serve_detect_exact<8, EL, X3>(p.c[6], mine); break;
-    default: serve_detect_exact<16, EL, X3>(p.c[7], mine); break;
+    case 7: serve_detect_exact<16, EL, X3>(p.c[7], mine); break;
+    default: serve_detect_exact<32, EL, X3>(p.c[8], mine); break;
   }
 }
 

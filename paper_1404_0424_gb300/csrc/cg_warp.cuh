@@ -245,6 +245,187 @@ __device__ __forceinline__ void quad_sum2(float& x0, float& x1) {
   x1 = s1 + c1;
 }
 
+__device__ __forceinline__ float warp_max(float x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, off));
+  return x;
+}
+__device__ __forceinline__ float quad_max(float x) {
+  x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, 1));
+  return fmaxf(x, __shfl_xor_sync(0xffffffffu, x, 2));
+}
+
+// ---------------------------------------------------------------------------
+// Exact power-of-two scaling of an instance
+// ---------------------------------------------------------------------------
+//
+// A split (hi + lo) FP16 operand keeps about 22 significant bits only while
+// |x| lies between about 2^-3 (below it the lo part is subnormal) and 65504
+// (above it hi overflows); BF16 has FP32's exponent range. Eq. 2 and
+// Algorithm 1 are invariant under exact power-of-two scaling: with
+// H' = 2^-e H, y' = 2^-f y, sigma' = 2^-2e sigma and N0' = 2^-2e N0, CG gives
+// v' = 2^(e-f) v (alpha' = 2^2e alpha, beta' = beta, the same breakdowns),
+// the trackers of Eqs. 10-13 give the same mu and rho, and CG-P with
+// t' = 2^-f t gives q' = 2^(e-f) q. So every instance is brought into the
+// FP16 range by one scale for H and one per right-hand side, and x_hat and
+// q are scaled back when they are stored.
+//
+// Fast path: e comes from the largest entry of H's first k-step, which the
+// loads deliver before the Gram's first product, and Y takes the same scale
+// (f = e, so x_hat needs none); T, read whole before CG-P starts, gets its
+// own per row. Inputs already in range (channels of roughly unit power)
+// keep scale 1 and run the unscaled code. Before CG starts, the largest
+// diagonal entry of the scaled Gram and ||b||^2 of every right-hand side
+// are checked against the range the FP16 split needs; an instance that
+// fails (a first k-step unlike the rest, or receive vectors on a scale of
+// their own) is formed again on a slow path with scales taken from every
+// entry (full_scale), with f per row. A = G + sigma I gets a scale of its
+// own in setup_a.
+
+// Exact 2^e for |e| <= 126.
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+// 2^e with e clamped to the normal range.
+__device__ __forceinline__ float pow2c(int e) { return pow2f(e < -126 ? -126 : e > 126 ? 126 : e); }
+
+// The scales of a lane, packed in one word: e (H' = 2^-e H) in bits 0-7,
+// f of rows g and g + 8 (2^-f) in bits 8-15 and 16-23, each in [-100, 100],
+// and in bit 24 whether any lane of the warp has a scale other than 1.
+struct InstScale {
+  int w;
+  __device__ __forceinline__ int e() const { return (w << 24) >> 24; }
+  __device__ __forceinline__ int f(int h) const { return h ? (w << 8) >> 24 : (w << 16) >> 24; }
+  __device__ __forceinline__ bool any() const { return (w >> 24) & 1; }
+  // 2^-2e, the factor of sigma and N0 (1 when no lane is scaled).
+  __device__ __forceinline__ float s2() const { return any() ? pow2c(-2 * e()) : 1.f; }
+  // 2^(f - e): x_hat of row g (h = 0) or g + 8 (h = 1) from the scaled CG.
+  __device__ __forceinline__ float xs(int h) const { return pow2c(f(h) - e()); }
+  // Packs e, f0, f1 (warp-collective: sets the any bit).
+  __device__ __forceinline__ static InstScale make(int e, int f0, int f1) {
+    InstScale s;
+    s.w = (e & 255) | ((f0 & 255) << 8) | ((f1 & 255) << 16);
+    if (__any_sync(0xffffffffu, s.w != 0)) s.w |= 1 << 24;
+    return s;
+  }
+};
+
+// floor(log2 m) for normal m > 0.
+__device__ __forceinline__ int exp2_floor(float m) { return ((__float_as_int(m) >> 23) & 0xff) - 127; }
+
+// 0 when lo <= m <= hi (or m is 0 or not finite: nothing to go by), else
+// the e that puts m 2^-e in [2^t, 2^(t+1)).
+__device__ __forceinline__ int band_exp(float m, float lo, float hi, int t) {
+  if ((m >= lo && m <= hi) || !(m > 0.f) || !(m <= 3.0e38f)) return 0;
+  const int e = exp2_floor(m) - t;
+  return e < -100 ? -100 : e > 100 ? 100 : e;
+}
+
+// Range of the largest component in H's first k-step that runs unscaled,
+// [1/2, 8], and where a scaled one is put, [2, 4); ||t||^2 of a row of T:
+// [2^-4, 2^12] and [4, 16) (even exponent offsets, so that the scale of t
+// itself is a power of two). CN(0,1) channels and unit-energy symbols fall
+// in the first ranges.
+constexpr float kHLo = 0.5f, kHHi = 8.f;
+constexpr int kHTarget = 1;
+constexpr float kTLo = 0.0625f, kTHi = 4096.f;
+constexpr int kTTarget = 2;
+
+// Range the fast path needs before CG starts: the largest diagonal entry of
+// the scaled Gram G' between 2^-8 B (below, H's entries would be near or
+// under FP16's lo-part floor) and 2^26 (above, some entry of H' is near or
+// past FP16's largest value), and ||b'||^2 of a right-hand side 0 or
+// between 1 and 2^26 (b' starts the CG direction, which goes through the
+// FP16 split).
+constexpr float kColMsLo = 0.00390625f;
+constexpr float kGHi = 67108864.f;
+constexpr float kRLo = 1.f, kRHi = 67108864.f;
+
+// Fast-path scale from H's first k-step (h as from load_h_ks /
+// ring_gram_read): Y takes the same e.
+template <int UT>
+__device__ __forceinline__ InstScale scale_from_ks(const float2 (&h)[WarpCfg<UT>::MT][4]) {
+  constexpr int MT = WarpCfg<UT>::MT;
+  float mh = 0.f;
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mh = fmaxf(mh, fmaxf(fabsf(h[m][k].x), fabsf(h[m][k].y)));
+  // the warp's largest entry is in range when every lane's is, or (a lane
+  // whose entries are all zero, as past B) its entries are 0
+  const bool in = (mh >= kHLo && mh <= kHHi) || mh == 0.f;
+  int e = 0;
+  if (!__all_sync(0xffffffffu, in)) e = band_exp(warp_max(mh), kHLo, kHHi, kHTarget);
+  InstScale sc;
+  sc.w = (e & 255) | ((e & 255) << 8) | ((e & 255) << 16) | (e != 0 ? 1 << 24 : 0);
+  return sc;
+}
+
+// Slow-path scales from every entry: e puts the root mean square of H's
+// entries in [1, 2), f that of each right-hand-side row of Y in [1, 2)
+// (MF; else f = e). The largest entry of H is then below 2^7.5 and that of a
+// row below 2^5. Means are taken after dividing by the largest power of two
+// below the largest entry, so that no square overflows or underflows.
+__device__ __forceinline__ int rms_exp(const float2* p, int n) {
+  const int lane = threadIdx.x & 31;
+  float mx = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float2 v = p[i];
+    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  mx = warp_max(mx);
+  if (!(mx > 0.f) || !(mx <= 3.0e38f)) return 0;
+  const int e0 = exp2_floor(mx);
+  const float s0 = pow2c(-e0);
+  float s = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float2 v = p[i];
+    s = fmaf(v.x * s0, v.x * s0, fmaf(v.y * s0, v.y * s0, s));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  const int e = e0 + (exp2_floor(s / float(n)) >> 1);
+  return e < -100 ? -100 : e > 100 ? 100 : e;
+}
+
+// Out of line: it runs only for instances the fast path hands back.
+template <bool MF>
+__device__ __noinline__ InstScale full_scale(const float2* H, const float2* Y, int B, int U,
+                                                int R) {
+  const int g = (threadIdx.x & 31) >> 2;
+  const int e = rms_exp(H, B * U);
+  int f0 = e, f1 = e;
+  if constexpr (MF) {
+    f0 = f1 = 0;
+    for (int r = 0; r < R; ++r) {
+      const int f = rms_exp(Y + int64_t(r) * B, B);
+      if (r == g) f0 = f;
+      if (r == g + 8) f1 = f;
+    }
+  }
+  return InstScale::make(e, f0, f1);
+}
+
+// h *= sh, y rows *= sy0 (row g: y[0], y[2]) and sy1 (row g + 8: y[1], y[3]).
+// Every k-step goes through it, also at scale 1: one copy of the Gram loop
+// runs faster than an unscaled and a scaled one side by side.
+template <int UT, bool MF>
+__device__ __forceinline__ void apply_scale(float2 (&h)[WarpCfg<UT>::MT][4], float2 (&y)[4],
+                                            float sh, float sy0, float sy1) {
+#pragma unroll
+  for (int m = 0; m < WarpCfg<UT>::MT; ++m)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[m][k] = make_float2(h[m][k].x * sh, h[m][k].y * sh);
+  if constexpr (MF) {
+    y[0] = make_float2(y[0].x * sy0, y[0].y * sy0);
+    y[2] = make_float2(y[2].x * sy0, y[2].y * sy0);
+    y[1] = make_float2(y[1].x * sy1, y[1].y * sy1);
+    y[3] = make_float2(y[3].x * sy1, y[3].y * sy1);
+  }
+}
+
+// Status returned by a fast-path finish whose instance must be formed again
+// with full_scale (nothing was stored); statuses are >= 0.
+constexpr int kRedo = -1;
+
 // ---------------------------------------------------------------------------
 // Loads of one k-step (antennas b0 = 8 ks + 2 t and b0 + 1)
 // ---------------------------------------------------------------------------
@@ -384,7 +565,8 @@ struct WarpCg {
   float D[NB][2];
   float rrn[2];
   bool active[2], broke[2];
-  int kd[2];  // iterations completed per row
+  int kd[2];      // iterations completed per row
+  float es = 1.f;  // factor of the products with the fragments (setup_a)
 
   // Fragment index of (ks, nt, b, part) in the shared slice.
   __device__ __forceinline__ static int fidx(int ks, int nt, int b, int part) {
@@ -393,11 +575,29 @@ struct WarpCg {
 
   // Writes A = G + sigma I as B fragments (from the Gram accumulators) and
   // returns D = diag(A) and G_ii at the lane's positions. Row 8 nt + g of
-  // the Gram is row half nt % 2 of m-tile nt / 2.
-  __device__ __forceinline__ static void setup_a(const GramAcc<UT>& Gr, const GramAcc<UT>& Gi,
-                                                 float sigma, uint2* frag, float (&Dout)[NB][2],
-                                                 float (&Gd)[NB][2]) {
+  // the Gram is row half nt % 2 of m-tile nt / 2. The fragments hold
+  // 2^-a A, with a = 0 unless the largest diagonal entry (which bounds every
+  // entry of the positive definite A) lies outside [2^-2, 2^13]; the return
+  // value is 2^a, the factor that products with the fragments need. gmax
+  // gets the largest diagonal entry of G (warp-uniform).
+  __device__ __forceinline__ static float setup_a(const GramAcc<UT>& Gr, const GramAcc<UT>& Gi,
+                                                  float sigma, uint2* frag, float (&Dout)[NB][2],
+                                                  float (&Gd)[NB][2], float& gmax) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float mg = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float gd = __shfl_sync(0xffffffffu, Gr[nt >> 1][nt][2 * (nt & 1) + c],
+                                     4 * (2 * t + c) + t);
+        Gd[nt][c] = gd;
+        Dout[nt][c] = gd + sigma;
+        mg = fmaxf(mg, gd);
+      }
+    gmax = quad_max(mg);
+    const int a = band_exp(gmax + sigma, 0.25f, 8192.f, 10);
+    const float sa = pow2f(-a);
 #pragma unroll
     for (int ks = 0; ks < NB; ++ks)
 #pragma unroll
@@ -422,22 +622,47 @@ struct WarpCg {
             re = Gr[m][ks][d] + (diag ? sigma : 0.f);
             im = diag ? 0.f : -Gi[m][ks][d];
           }
+          re *= sa;
+          im *= sa;
           frag[fidx(ks, nt, b, 0) * 32 + lane] = split_c<EL>(make_float2(re, im));
           if constexpr (STORE_IM)
             frag[fidx(ks, nt, b, 1) * 32 + lane] = split_c<EL>(make_float2(-im, re));
         }
+    return pow2f(a);
+  }
+
+  // matvec, times the fragments' factor es when it is not 1.
+  __device__ __forceinline__ void matvec_s(const uint2* frag, float es, float (&Er)[NB][4],
+                                           float (&Ei)[NB][4]) const {
+    matvec(frag, Er, Ei);
+    if (es != 1.f) {
 #pragma unroll
-    for (int nt = 0; nt < NB; ++nt)
+      for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const float gd = __shfl_sync(0xffffffffu, Gr[nt >> 1][nt][2 * (nt & 1) + c],
-                                     4 * (2 * t + c) + t);
-        Gd[nt][c] = gd;
-        Dout[nt][c] = gd + sigma;
-      }
+        for (int k = 0; k < 4; ++k) {
+          Er[nt][k] *= es;
+          Ei[nt][k] *= es;
+        }
+    }
+  }
+
+  // One fragment of A from shared memory. With VOL the fragments are read at
+  // every product as volatile loads, so that the compiler does not hoist all
+  // of them (64 registers per lane at 32 users) out of the CG and tracker
+  // loops into registers that are needed for the vectors.
+  template <bool VOL>
+  __device__ __forceinline__ static uint2 lds_frag(const uint2* q) {
+    if constexpr (VOL) {
+      uint2 v;
+      asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(smem_addr(q)));
+      return v;
+    } else {
+      return *q;
+    }
   }
 
   // e = A p for every right-hand side row: E[nt][d] in accumulator layout.
+  template <bool VOL = (UT == 32)>
   __device__ __forceinline__ void matvec(const uint2* frag, float (&Er)[NB][4],
                                          float (&Ei)[NB][4]) const {
     const int lane = threadIdx.x & 31;
@@ -459,12 +684,12 @@ struct WarpCg {
       float ih[4] = {0.f, 0.f, 0.f, 0.f}, ix[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int ks = 0; ks < NB; ++ks) {
-        const uint2 r0 = frag[fidx(ks, nt, 0, 0) * 32 + lane];
-        const uint2 r1 = frag[fidx(ks, nt, 1, 0) * 32 + lane];
+        const uint2 r0 = lds_frag<VOL>(frag + fidx(ks, nt, 0, 0) * 32 + lane);
+        const uint2 r1 = lds_frag<VOL>(frag + fidx(ks, nt, 1, 0) * 32 + lane);
         uint2 i0, i1;
         if constexpr (STORE_IM) {
-          i0 = frag[fidx(ks, nt, 0, 1) * 32 + lane];
-          i1 = frag[fidx(ks, nt, 1, 1) * 32 + lane];
+          i0 = lds_frag<VOL>(frag + fidx(ks, nt, 0, 1) * 32 + lane);
+          i1 = lds_frag<VOL>(frag + fidx(ks, nt, 1, 1) * 32 + lane);
         } else {  // i (re, im) = (-im, re): swap the halves, negate the new low one
           i0 = make_uint2(swap_halves(r0.x) ^ 0x8000u, swap_halves(r0.y) ^ 0x8000u);
           i1 = make_uint2(swap_halves(r1.x) ^ 0x8000u, swap_halves(r1.y) ^ 0x8000u);
@@ -487,9 +712,8 @@ struct WarpCg {
   // Lines 7-14 of Algorithm 1. res holds b on entry; rows >= R are
   // inactive from the start. With TRACK, alpha_k and beta_k of every row are
   // kept in sAB[(k - 1) * 16 + row] for the tracker (tracker_l below).
-  template <bool TRACK>
-  __device__ __forceinline__ void run(const uint2* frag, float2* sAB, int R, int K) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  // Line 7: v = 0, p = r = b (res holds b), ||r||^2 of every row.
+  __device__ __forceinline__ void init() {
     float s[2] = {0.f, 0.f};
 #pragma unroll
     for (int h = 0; h < 2; ++h)
@@ -503,9 +727,16 @@ struct WarpCg {
                       fmaf(res[h][nt][c].y, res[h][nt][c].y, s[h]));
         }
     quad_sum2(s[0], s[1]);
+    rrn[0] = s[0];
+    rrn[1] = s[1];
+  }
+
+  // Lines 8-14 after init().
+  template <bool TRACK>
+  __device__ __forceinline__ void run(const uint2* frag, float2* sAB, int R, int K) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      rrn[h] = s[h];
       active[h] = (g + 8 * h) < R;
       broke[h] = false;
       kd[h] = 0;
@@ -538,7 +769,9 @@ struct WarpCg {
           active[h] = false;
           broke[h] = true;
         }
-        alpha[h] = active[h] ? __fdividef(rrn[h], pe[h]) : 0.f;
+        // the product came out as 2^-a A p (es = 2^a): alpha = r^H r / (es p^H E)
+        alpha[h] = active[h] ? __fdividef(rrn[h], pe[h] * es) : 0.f;
+        const float ae = alpha[h] * es;
 #pragma unroll
         for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
@@ -546,8 +779,8 @@ struct WarpCg {
             if (active[h]) {
               v[h][nt][c].x = fmaf(alpha[h], p[h][nt][c].x, v[h][nt][c].x);
               v[h][nt][c].y = fmaf(alpha[h], p[h][nt][c].y, v[h][nt][c].y);
-              res[h][nt][c].x = fmaf(-alpha[h], Er[nt][2 * h + c], res[h][nt][c].x);
-              res[h][nt][c].y = fmaf(-alpha[h], Ei[nt][2 * h + c], res[h][nt][c].y);
+              res[h][nt][c].x = fmaf(-ae, Er[nt][2 * h + c], res[h][nt][c].x);
+              res[h][nt][c].y = fmaf(-ae, Ei[nt][2 * h + c], res[h][nt][c].y);
             }
             rrnew[h] = fmaf(res[h][nt][c].x, res[h][nt][c].x,
                             fmaf(res[h][nt][c].y, res[h][nt][c].y, rrnew[h]));
@@ -600,7 +833,7 @@ struct WarpCg {
 #pragma unroll
           for (int c = 0; c < 2; ++c) p[h][nt][c] = v[h][nt][c];
       float Er[NB][4], Ei[NB][4];
-      matvec(frag, Er, Ei);
+      matvec_s(frag, es, Er, Ei);
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -615,29 +848,43 @@ struct WarpCg {
 
   // Eq. 10 for right-hand side `row` (alpha_k, beta_k in sAB, kdone
   // iterations), then B = L_K G, C = L_K G L_K^H and, for the lane's matrix
-  // rows g + 8 hh (users at positions g + 8 hh; UT <= 16),
+  // rows 16 m + g + 8 hh (the users at those positions),
   //   mu = Re B_ii,  nu^2 = Es sum_{j != i} |B_ij|^2 + N0 C_ii,  rho = mu^2 / nu^2.
   // L_k is a polynomial in A with real coefficients, so it commutes with A
-  // and A (L_{k-1} - L_{k-2}) = (L_{k-1} - L_{k-2}) A: the 16 rows of the
+  // and A (L_{k-1} - L_{k-2}) = (L_{k-1} - L_{k-2}) A: 16 rows of the
   // difference pass through matvec exactly like 16 right-hand sides, and
-  // every product of the recursion runs on the tensor cores. Rows and
-  // columns are in position order; p is overwritten.
+  // every product of the recursion runs on the tensor cores. Each row of the
+  // recursion depends on the same row only, so 32 users run it as two
+  // halves of 16 rows (m = 0, 1). Rows and columns are in position order;
+  // p is overwritten.
+  //
+  // The recursion is carried as L and the differences D1 = L_{k-1} - L_{k-2},
+  // D2 = L_{k-2} - L_{k-3}: D_k = c1 D1 - alpha_k D1 A - c2 D2, L_k = L_{k-1} + D_k.
+  // The L_k are of the order of alpha_1 (L_1 = alpha_1 I), so they are held
+  // as 2^-s L (2^s <= alpha_1 < 2^(s+1)), which is also what enters the FP16
+  // split; D1 lives in p, the operand of the product. With Ls (one 16-row
+  // block of L, 32 entries per lane) L lives in shared memory, which leaves
+  // the registers to D1, D2 and the product.
   __device__ __forceinline__ void exact_sinr(const uint2* frag, const float2* sAB, int row,
-                                             int kdone, float sigma, float N0, float Es,
-                                             float (&mu)[2], float (&rho)[2]) {
-    static_assert(UT <= 16, "the warp exact tracker holds one 16 x 16 tile");
+                                             int kdone, float sigma, float N0, float Es, int m,
+                                             float2* Ls, float (&mu)[2], float (&rho)[2]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    float2 L1[2][NB][2], L2[2][NB][2], L3[2][NB][2];
+    float2 Lr[2][NB][2], D2[2][NB][2];
     const float a1 = sAB[row].x;
+    const int sl = (a1 > 0.f && a1 <= 3.0e38f) ? exp2_floor(a1) : 0;
+    const float a1s = a1 * pow2c(-sl);  // alpha_1 2^-s, in [1, 2)
+    auto lidx = [&](int h, int nt, int c) { return ((h * NB + nt) * 2 + c) * 32 + lane; };
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const bool diag = (h == nt) && (g == 2 * t + c);
-          L1[h][nt][c] = make_float2(diag ? a1 : 0.f, 0.f);  // L_1 = alpha_1 I
-          L2[h][nt][c] = L3[h][nt][c] = make_float2(0.f, 0.f);
+          const bool diag = 8 * nt + 2 * t + c == 16 * m + 8 * h + g;
+          const float2 l1 = make_float2(diag ? a1s : 0.f, 0.f);  // 2^-s L_1
+          p[h][nt][c] = l1;                                     // 2^-s (L_1 - L_0)
+          D2[h][nt][c] = make_float2(0.f, 0.f);
+          if (Ls) Ls[lidx(h, nt, c)] = l1; else Lr[h][nt][c] = l1;
         }
     for (int k = 2; k <= kdone; ++k) {
       const float2 abk = sAB[(k - 1) * 16 + row], ab1 = sAB[(k - 2) * 16 + row];
@@ -645,41 +892,38 @@ struct WarpCg {
       const float ak = abk.x;
       const float c1 = ak * (1.f + ab1.y) / ab1.x;
       const float c2 = ak * ab2.y / ab2.x;
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int nt = 0; nt < NB; ++nt)
-#pragma unroll
-          for (int c = 0; c < 2; ++c)
-            p[h][nt][c] = make_float2(L1[h][nt][c].x - L2[h][nt][c].x,
-                                      L1[h][nt][c].y - L2[h][nt][c].y);
+      const float ake = ak * es;
       float Er[NB][4], Ei[NB][4];
-      matvec(frag, Er, Ei);  // (L_{k-1} - L_{k-2}) A
+      matvec<true>(frag, Er, Ei);  // 2^-s D1 2^-a A
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
-            const float2 d = p[h][nt][c];
-            const float2 l2 = L2[h][nt][c], l3 = L3[h][nt][c];
-            float2 ln;
-            ln.x = L1[h][nt][c].x + c1 * d.x - ak * Er[nt][2 * h + c] - c2 * (l2.x - l3.x);
-            ln.y = L1[h][nt][c].y + c1 * d.y - ak * Ei[nt][2 * h + c] - c2 * (l2.y - l3.y);
-            L3[h][nt][c] = l2;
-            L2[h][nt][c] = L1[h][nt][c];
-            L1[h][nt][c] = ln;
+            const float2 d1 = p[h][nt][c], d2 = D2[h][nt][c];
+            float2 dn;
+            dn.x = c1 * d1.x - ake * Er[nt][2 * h + c] - c2 * d2.x;
+            dn.y = c1 * d1.y - ake * Ei[nt][2 * h + c] - c2 * d2.y;
+            D2[h][nt][c] = d1;
+            p[h][nt][c] = dn;
+            if (Ls) {
+              const float2 l = Ls[lidx(h, nt, c)];
+              Ls[lidx(h, nt, c)] = make_float2(l.x + dn.x, l.y + dn.y);
+            } else {
+              Lr[h][nt][c] = make_float2(Lr[h][nt][c].x + dn.x, Lr[h][nt][c].y + dn.y);
+            }
           }
     }
-    // B = L_K A - sigma L_K
+    // 2^-s B = 2^-s L_K A - sigma 2^-s L_K
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) p[h][nt][c] = L1[h][nt][c];
+        for (int c = 0; c < 2; ++c) p[h][nt][c] = Ls ? Ls[lidx(h, nt, c)] : Lr[h][nt][c];
     float Er[NB][4], Ei[NB][4];
-    matvec(frag, Er, Ei);
+    matvec<true>(frag, Er, Ei);
     float dg[2] = {0.f, 0.f}, itf[2] = {0.f, 0.f}, cc[2] = {0.f, 0.f};
 #pragma unroll
     for (int h = 0; h < 2; ++h)
@@ -687,10 +931,10 @@ struct WarpCg {
       for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const float2 l = L1[h][nt][c];
-          const float bx = fmaf(-sigma, l.x, Er[nt][2 * h + c]);
-          const float by = fmaf(-sigma, l.y, Ei[nt][2 * h + c]);
-          const bool diag = (h == nt) && (g == 2 * t + c);
+          const float2 l = p[h][nt][c];
+          const float bx = fmaf(-sigma, l.x, Er[nt][2 * h + c] * es);
+          const float by = fmaf(-sigma, l.y, Ei[nt][2 * h + c] * es);
+          const bool diag = 8 * nt + 2 * t + c == 16 * m + 8 * h + g;
           if (diag)
             dg[h] += bx;
           else
@@ -700,11 +944,12 @@ struct WarpCg {
     quad_sum2(dg[0], dg[1]);
     quad_sum2(itf[0], itf[1]);
     quad_sum2(cc[0], cc[1]);
+    const float s1 = pow2c(sl), s2 = s1 * s1;  // undo 2^-s (B, L) and 2^-2s (products)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      mu[h] = dg[h];
-      const float nu2 = fmaf(Es, itf[h], N0 * cc[h]);
-      rho[h] = nu2 > 0.f ? dg[h] * dg[h] / nu2 : 0.f;
+      mu[h] = dg[h] * s1;
+      const float nu2 = fmaf(Es, itf[h], N0 * cc[h]) * s2;
+      rho[h] = nu2 > 0.f ? mu[h] * mu[h] / nu2 : 0.f;
     }
   }
 
@@ -905,11 +1150,62 @@ __device__ __forceinline__ void store_row_detect(const DetItem& it, int r, int t
 // ahead (through L1), or predicated element loads for any layout.
 enum : int { LD_RING = 0, LD_VEC = 1, LD_ELEM = 2 };
 
-// Algorithm 1 line 5: G and b^T on the tensor cores.
+// k-steps 0..KS-1 through the ring; (h, y) already hold k-step 0.
+template <int UT, int EL, bool X3, bool MF>
+__device__ __forceinline__ void gram_ring_loop(const float2* H, const float2* Y, int B, int R,
+                                               int KS, unsigned char* ring,
+                                               float2 (&h)[WarpCfg<UT>::MT][4], float2 (&y)[4],
+                                               float sh, float sy0, float sy1, GramAcc<UT>& Gr,
+                                               GramAcc<UT>& Gi, VecAcc<UT>& Mr, VecAcc<UT>& Mn) {
+  for (int ks = 0;;) {
+    apply_scale<UT, MF>(h, y, sh, sy0, sy1);
+    gram_ks<UT, EL, X3, MF>(h, y, Gr, Gi, Mr, Mn);
+    if (++ks >= KS) break;
+    ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, ks + RING_STAGES - 1);
+    cp_wait<RING_STAGES - 1>();
+    ring_gram_read<UT, MF>(ring, ks, h, y);
+  }
+}
+
+// k-steps 0..KS-1 with register loads one k-step ahead (ping-pong); (ha, ya)
+// already hold k-step 0.
+template <int UT, int EL, bool X3, bool V, bool MF>
+__device__ __forceinline__ void gram_direct_loop(const float2* H, const float2* Y, int B, int U,
+                                                 int R, int KS, float2 (&ha)[WarpCfg<UT>::MT][4],
+                                                 float2 (&ya)[4], float sh, float sy0, float sy1,
+                                                 GramAcc<UT>& Gr, GramAcc<UT>& Gi,
+                                                 VecAcc<UT>& Mr, VecAcc<UT>& Mn) {
+  constexpr int MT = WarpCfg<UT>::MT;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float2 hb[MT][4], yb[4] = {};
+  for (int ks = 0; ks < KS; ks += 2) {
+    if constexpr (V) {
+      prefetch_h_block<UT>(H, B, ks + 1 + PF_GRAM);
+      prefetch_h_block<UT>(H, B, ks + 2 + PF_GRAM);
+    }
+    if (ks + 1 < KS) {
+      load_h_ks<UT, V>(H, B, U, ks + 1, g, t, hb);
+      if constexpr (MF) load_y_ks<V>(Y, B, R, ks + 1, g, t, yb);
+    }
+    apply_scale<UT, MF>(ha, ya, sh, sy0, sy1);
+    gram_ks<UT, EL, X3, MF>(ha, ya, Gr, Gi, Mr, Mn);
+    if (ks + 1 >= KS) break;
+    if (ks + 2 < KS) {
+      load_h_ks<UT, V>(H, B, U, ks + 2, g, t, ha);
+      if constexpr (MF) load_y_ks<V>(Y, B, R, ks + 2, g, t, ya);
+    }
+    apply_scale<UT, MF>(hb, yb, sh, sy0, sy1);
+    gram_ks<UT, EL, X3, MF>(hb, yb, Gr, Gi, Mr, Mn);
+  }
+}
+
+// Algorithm 1 line 5: G and b^T on the tensor cores, of H and Y scaled by
+// sc. Unless `given`, sc is first chosen from k-step 0 (scale_from_ks).
 template <int UT, int EL, bool X3, int LD, bool MF>
 __device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int B, int U, int R,
                                           unsigned char* ring, GramAcc<UT>& Gr, GramAcc<UT>& Gi,
-                                          VecAcc<UT>& Mr, VecAcc<UT>& Mn) {
+                                          VecAcc<UT>& Mr, VecAcc<UT>& Mn, InstScale& sc,
+                                          bool given) {
   constexpr int NB = UT / 8, MT = WarpCfg<UT>::MT;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
@@ -921,57 +1217,72 @@ __device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int 
       for (int m = 0; m < MT; ++m) Gr[m][nt][k] = Gi[m][nt][k] = 0.f;
     }
   const int KS = (B + 7) / 8;
+  constexpr bool V = LD == LD_VEC;
+  float2 h[MT][4], y[4] = {};
   if constexpr (LD == LD_RING) {
-    for (int ks = 0; ks < KS; ++ks) {
-      ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, ks + RING_STAGES - 1);
-      cp_wait<RING_STAGES - 1>();
-      float2 h[MT][4], y[4];
-      ring_gram_read<UT, MF>(ring, ks, h, y);
-      gram_ks<UT, EL, X3, MF>(h, y, Gr, Gi, Mr, Mn);
-    }
+    ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, RING_STAGES - 1);
+    cp_wait<RING_STAGES - 1>();
+    ring_gram_read<UT, MF>(ring, 0, h, y);
   } else {
-    constexpr bool V = LD == LD_VEC;
-    float2 ha[MT][4], ya[4] = {}, hb[MT][4], yb[4] = {};
     if constexpr (V)
 #pragma unroll
       for (int d = 1; d <= PF_GRAM; ++d) prefetch_h_block<UT>(H, B, d);
-    load_h_ks<UT, V>(H, B, U, 0, g, t, ha);
-    if constexpr (MF) load_y_ks<V>(Y, B, R, 0, g, t, ya);
-    for (int ks = 0; ks < KS; ks += 2) {  // ping-pong: loads run one k-step ahead
-      if constexpr (V) {
-        prefetch_h_block<UT>(H, B, ks + 1 + PF_GRAM);
-        prefetch_h_block<UT>(H, B, ks + 2 + PF_GRAM);
-      }
-      if (ks + 1 < KS) {
-        load_h_ks<UT, V>(H, B, U, ks + 1, g, t, hb);
-        if constexpr (MF) load_y_ks<V>(Y, B, R, ks + 1, g, t, yb);
-      }
-      gram_ks<UT, EL, X3, MF>(ha, ya, Gr, Gi, Mr, Mn);
-      if (ks + 1 >= KS) break;
-      if (ks + 2 < KS) {
-        load_h_ks<UT, V>(H, B, U, ks + 2, g, t, ha);
-        if constexpr (MF) load_y_ks<V>(Y, B, R, ks + 2, g, t, ya);
-      }
-      gram_ks<UT, EL, X3, MF>(hb, yb, Gr, Gi, Mr, Mn);
-    }
+    load_h_ks<UT, V>(H, B, U, 0, g, t, h);
+    if constexpr (MF) load_y_ks<V>(Y, B, R, 0, g, t, y);
   }
+  if (!given) sc = scale_from_ks<UT>(h);
+  const float sh = pow2f(-sc.e()), sy0 = pow2f(-sc.f(0)), sy1 = pow2f(-sc.f(1));
+  if constexpr (LD == LD_RING)
+    gram_ring_loop<UT, EL, X3, MF>(H, Y, B, R, KS, ring, h, y, sh, sy0, sy1, Gr, Gi, Mr, Mn);
+  else
+    gram_direct_loop<UT, EL, X3, V, MF>(H, Y, B, U, R, KS, h, y, sh, sy0, sy1, Gr, Gi, Mr, Mn);
+}
+
+// x[0] *= s0, x[1] *= s1 (rows g and g + 8 of the lane).
+template <int NB>
+__device__ __forceinline__ void scale_rows(float2 (&x)[2][NB][2], float s0, float s1) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float sh = h ? s1 : s0;
+        x[h][nt][c] = make_float2(x[h][nt][c].x * sh, x[h][nt][c].y * sh);
+      }
 }
 
 // Lines 7-19 and Eq. 4 of one instance whose Gram and matched filters are done.
 // Solvers of the warp bodies: CG (Algorithm 1) or the Neumann series (Sec. III-F).
 constexpr int SOLVE_CG = 0;
 constexpr int SOLVE_NEUMANN = 1;
-constexpr int SOLVE_CG_EXACT = 2;  // CG with the exact tracker of Eq. 10 (UT <= 16)
+constexpr int SOLVE_CG_EXACT = 2;  // CG with the exact tracker of Eq. 10
+
+// sc: the instance's scales; the Gram and matched filters are those of the
+// scaled H and Y, so sigma and N0 are scaled by 2^-2e here and x_hat by
+// 2^(f - e) when it is stored. With CHECK (the fast path), an instance
+// whose scaled Gram or matched filter lies outside the range the FP16 split
+// needs returns kRedo before anything is stored.
+//
+// The exact tracker with 32 users keeps x_hat and the gathered mu, rho in the
+// idle load ring (scratch) while the L_k recursion holds the registers; its
+// kernels issue the next instance's first load stages only after this.
+template <int UT, int SOLVER>
+struct ExactStage {
+  static constexpr bool kOn = SOLVER == SOLVE_CG_EXACT && UT == 32;
+};
 
 template <int UT, int EL, bool VEC, int SOLVER = SOLVE_CG>
 __device__ __forceinline__ int detect_warp_finish(const DetItem& it, uint2* frag, float2* sAB,
                                                   const GramAcc<UT>& Gr, const GramAcc<UT>& Gi,
-                                                  const VecAcc<UT>& Mr, const VecAcc<UT>& Mn) {
+                                                  const VecAcc<UT>& Mr, const VecAcc<UT>& Mn,
+                                                  InstScale sc, bool check,
+                                                  unsigned char* scratch) {
   constexpr int NB = UT / 8;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   WarpCg<UT, EL> cg;
-  float Gd[NB][2];
-  WarpCg<UT, EL>::setup_a(Gr, Gi, it.sigma, frag, cg.D, Gd);
+  float Gd[NB][2], gmax;
+  cg.es = WarpCg<UT, EL>::setup_a(Gr, Gi, it.sigma * sc.s2(), frag, cg.D, Gd, gmax);
 #pragma unroll
   for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
@@ -979,6 +1290,14 @@ __device__ __forceinline__ int detect_warp_finish(const DetItem& it, uint2* frag
 #pragma unroll
       for (int c = 0; c < 2; ++c)
         cg.res[hh][nt][c] = make_float2(Mr[nt][2 * hh + c], -Mn[nt][2 * hh + c]);
+  cg.init();
+  if (check) {
+    bool ok = gmax == 0.f || (gmax >= kColMsLo * float(it.B) && gmax <= kGHi);
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh)
+      ok = ok && (cg.rrn[hh] == 0.f || (cg.rrn[hh] >= kRLo && cg.rrn[hh] <= kRHi));
+    if (!__all_sync(0xffffffffu, ok)) return kRedo;
+  }
   __syncwarp();
   if constexpr (SOLVER == SOLVE_NEUMANN) {
     // x_hat only: the soft outputs of this path are those of CG
@@ -991,6 +1310,7 @@ __device__ __forceinline__ int detect_warp_finish(const DetItem& it, uint2* frag
         one[nt][c] = 1.f;
         zero[nt][c] = 0.f;
       }
+    if (sc.any()) scale_rows<NB>(cg.v, sc.xs(0), sc.xs(1));
     int nflags = 0;
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh)
@@ -1005,45 +1325,85 @@ __device__ __forceinline__ int detect_warp_finish(const DetItem& it, uint2* frag
   int flags = 0;
   const float cq = sqrtf(3.f * it.Es / (2.f * float((1 << it.q) - 1)));
   float rho[NB][2];
+  const float n0s = it.N0 * sc.s2(), sigs = it.sigma * sc.s2();  // scaled N0 and sigma
 #pragma unroll
   for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
-    for (int c = 0; c < 2; ++c) rho[nt][c] = Gd[nt][c] / it.N0;  // Eq. 13
+    for (int c = 0; c < 2; ++c) rho[nt][c] = Gd[nt][c] / n0s;  // Eq. 13
   // exact tracker: mu and rho of every right-hand side, gathered into the
-  // lanes that store its row (position P = 8 nt + 2 t + c of row r is held
-  // after exact_sinr by the lanes with g = 2 t + c, as their row half nt)
+  // lanes that store its row (position P = 16 m + 8 h + g' = 8 nt + 2 t + c
+  // of row r is held after exact_sinr of half m by the lanes with g' = 2 t + c,
+  // as their row h = nt - 2 m)
   float emu[2][NB][2], erho[2][NB][2];
+  constexpr bool XS = ExactStage<UT, SOLVER>::kOn;
+  static_assert(!XS || 2 * NB * 2 * 32 * 24 <= WarpCfg<UT>::RING_BYTES, "scratch fits the ring");
+  // scratch layout (XS): x_hat, then mu and rho, each entry [h][nt][c] of a
+  // lane at ((h NB + nt) 2 + c) 32 + lane
+  float2* xs_v = reinterpret_cast<float2*>(scratch);
+  float* xs_mu = reinterpret_cast<float*>(scratch + 2 * NB * 2 * 32 * 8);
+  float* xs_rho = xs_mu + 2 * NB * 2 * 32;
+  // one 16-row block of L_k for exact_sinr (XS), else none (registers)
+  float2* xs_L = XS ? reinterpret_cast<float2*>(xs_rho + 2 * NB * 2 * 32) : nullptr;
   if constexpr (SOLVER == SOLVE_CG_EXACT) {
+    constexpr int NH = UT == 32 ? 2 : 1;  // halves of 16 matrix rows
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
       for (int nt = 0; nt < NB; ++nt)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) emu[hh][nt][c] = erho[hh][nt][c] = 0.f;
+        for (int c = 0; c < 2; ++c) {
+          emu[hh][nt][c] = erho[hh][nt][c] = 0.f;
+          if constexpr (XS) {
+            const int o = ((hh * NB + nt) * 2 + c) * 32 + lane;
+            xs_v[o] = cg.v[hh][nt][c];
+            xs_mu[o] = xs_rho[o] = 0.f;
+          }
+        }
     for (int r = 0; r < it.R; ++r) {
       const bool upper = r >= 8;  // row half of r (register arrays take constant indices)
       const int kdone = __shfl_sync(0xffffffffu, upper ? cg.kd[1] : cg.kd[0], 4 * (r & 7));
-      float m2[2] = {0.f, 0.f}, r2[2] = {0.f, 0.f};
-      if (kdone > 0) cg.exact_sinr(frag, sAB, r, kdone, it.sigma, it.N0, it.Es, m2, r2);
 #pragma unroll
-      for (int nt = 0; nt < NB; ++nt)
+      for (int m = 0; m < NH; ++m) {
+        float m2[2] = {0.f, 0.f}, r2[2] = {0.f, 0.f};
+        if (kdone > 0) cg.exact_sinr(frag, sAB, r, kdone, sigs, n0s, it.Es, m, xs_L, m2, r2);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int src = 4 * (2 * t + c) + t;
-          const float mv = __shfl_sync(0xffffffffu, m2[nt], src);
-          const float rv = __shfl_sync(0xffffffffu, r2[nt], src);
-          if (g == (r & 7)) {
-            if (upper) {
-              emu[1][nt][c] = mv;
-              erho[1][nt][c] = rv;
-            } else {
-              emu[0][nt][c] = mv;
-              erho[0][nt][c] = rv;
+        for (int nt = 2 * m; nt < (NB < 2 * m + 2 ? NB : 2 * m + 2); ++nt)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int src = 4 * (2 * t + c) + t;
+            const float mv = __shfl_sync(0xffffffffu, m2[nt - 2 * m], src);
+            const float rv = __shfl_sync(0xffffffffu, r2[nt - 2 * m], src);
+            if (g == (r & 7)) {
+              if constexpr (XS) {
+                const int o = (((upper ? 1 : 0) * NB + nt) * 2 + c) * 32 + lane;
+                xs_mu[o] = mv;
+                xs_rho[o] = rv;
+              } else if (upper) {
+                emu[1][nt][c] = mv;
+                erho[1][nt][c] = rv;
+              } else {
+                emu[0][nt][c] = mv;
+                erho[0][nt][c] = rv;
+              }
             }
           }
-        }
+      }
+    }
+    if constexpr (XS) {
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int o = ((hh * NB + nt) * 2 + c) * 32 + lane;
+            cg.v[hh][nt][c] = xs_v[o];
+            emu[hh][nt][c] = xs_mu[o];
+            erho[hh][nt][c] = xs_rho[o];
+          }
     }
   }
+  if (sc.any()) scale_rows<NB>(cg.v, sc.xs(0), sc.xs(1));
 #pragma unroll
   for (int hh = 0; hh < 2; ++hh) {
     const int r = g + 8 * hh;
@@ -1110,33 +1470,66 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
   int64_t cur = warp_first(src, int64_t(blockIdx.x) * (blockDim.x >> 5) + warp);
   bool vec = false;
+  // kLate: the next instance's first stages are issued after the finish,
+  // which uses the ring as scratch (ExactStage)
+  constexpr bool kLate = ExactStage<UT, SOLVER>::kOn;
   if (cur >= 0) {
     const DetItem it = det_item(src, cur);
     vec = detect_vec<UT>(it);
     if (vec) ring_gram_prologue<UT, true>(ring, it.H, it.Y, it.B, it.R);
   }
+  // An instance the fast path hands back (kRedo) runs once more with scales
+  // from every entry and element loads (redo.w != 0), while the ring keeps
+  // the first stages of the next instance (next, nvec), which was claimed
+  // on the first pass.
+  InstScale redo;
+  redo.w = 0;
+  int64_t next = -1;
+  bool nvec = false;
   while (cur >= 0) {
     GramAcc<UT> Gr, Gi;
     VecAcc<UT> Mr, Mn;
+    InstScale sc = redo;
+    const bool again = redo.w != 0;
     {
       const DetItem it = det_item(src, cur);
-      if (vec)
-        warp_gram<UT, EL, X3, LD_RING, true>(it.H, it.Y, it.B, it.U, it.R, ring, Gr, Gi, Mr, Mn);
+      if (vec && !again)
+        warp_gram<UT, EL, X3, LD_RING, true>(it.H, it.Y, it.B, it.U, it.R, ring, Gr, Gi, Mr, Mn,
+                                             sc, false);
       else
-        warp_gram<UT, EL, X3, LD_ELEM, true>(it.H, it.Y, it.B, it.U, it.R, ring, Gr, Gi, Mr, Mn);
+        warp_gram<UT, EL, X3, LD_ELEM, true>(it.H, it.Y, it.B, it.U, it.R, ring, Gr, Gi, Mr, Mn,
+                                             sc, again);
     }
-    int64_t next = warp_next_early(src, cur, nw);
-    bool nvec = false;
-    if (next >= 0) {
-      const DetItem nit = det_item(src, next);
-      nvec = detect_vec<UT>(nit);
-      if (nvec) ring_gram_prologue<UT, true>(ring, nit.H, nit.Y, nit.B, nit.R);
+    if (!again) {
+      next = warp_next_early(src, cur, nw);
+      nvec = false;
+      if (next >= 0) {
+        const DetItem nit = det_item(src, next);
+        nvec = detect_vec<UT>(nit);
+        if (nvec && !kLate) ring_gram_prologue<UT, true>(ring, nit.H, nit.Y, nit.B, nit.R);
+      }
     }
     int st;
     {
       const DetItem it = det_item(src, cur);
-      st = vec ? detect_warp_finish<UT, EL, true, SOLVER>(it, frag, sAB, Gr, Gi, Mr, Mn)
-               : detect_warp_finish<UT, EL, false, SOLVER>(it, frag, sAB, Gr, Gi, Mr, Mn);
+      st = (vec && !again)
+               ? detect_warp_finish<UT, EL, true, SOLVER>(it, frag, sAB, Gr, Gi, Mr, Mn, sc, true,
+                                                          ring)
+               : detect_warp_finish<UT, EL, false, SOLVER>(it, frag, sAB, Gr, Gi, Mr, Mn, sc,
+                                                           !again, ring);
+      if (st == kRedo) {
+        redo = full_scale<true>(it.H, it.Y, it.B, it.U, it.R);
+        redo.w |= 1 << 25;  // marks the second pass even when every scale is 1
+        continue;
+      }
+    }
+    redo.w = 0;
+    if constexpr (kLate) {
+      __syncwarp();  // every lane is done with the scratch
+      if (next >= 0 && nvec) {
+        const DetItem nit = det_item(src, next);
+        ring_gram_prologue<UT, true>(ring, nit.H, nit.Y, nit.B, nit.R);
+      }
     }
     __syncwarp();
     if constexpr (SrcTraits<Src>::kDyn) {
@@ -1161,15 +1554,18 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
 // ---------------------------------------------------------------------------
 
 // Lines 7-14 with b = t, ||q||, then line 20 (q = H v) of one instance whose
-// Gram is done.
+// Gram is done. hsc holds the scale e of H; each row of T gets its own f
+// here: the CG runs on 2^-e H, 2^-f t and 2^-2e sigma, giving v' = 2^(2e - f) v,
+// and q = 2^(f - e) (2^-e H) v', ||q|| = 2^(f - e) ||2^-e H v'||. With CHECK
+// (the fast path), an instance whose scaled Gram lies outside the range the
+// FP16 split needs returns kRedo before anything is stored.
 template <int UT, int EL, bool X3, bool VEC, int SOLVER = SOLVE_CG>
 __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* frag,
-                                                   const GramAcc<UT>& Gr, const GramAcc<UT>& Gi) {
+                                                   const GramAcc<UT>& Gr, const GramAcc<UT>& Gi,
+                                                   InstScale hsc, bool check) {
   constexpr int NB = UT / 8;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   WarpCg<UT, EL> cg;
-  float Gd[NB][2];
-  WarpCg<UT, EL>::setup_a(Gr, Gi, it.sigma, frag, cg.D, Gd);
 #pragma unroll
   for (int hh = 0; hh < 2; ++hh) {
     const int r = g + 8 * hh;
@@ -1181,6 +1577,20 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
         const int u = pos_user<UT>(8 * nt + 2 * t + c);
         cg.res[hh][nt][c] = (r < it.R && u < it.U) ? tr[u] : make_float2(0.f, 0.f);
       }
+  }
+  float Gd[NB][2], gmax;
+  cg.es = WarpCg<UT, EL>::setup_a(Gr, Gi, it.sigma * hsc.s2(), frag, cg.D, Gd, gmax);
+  if (check && !(gmax == 0.f || (gmax >= kColMsLo * float(it.B) && gmax <= kGHi))) return kRedo;
+  cg.init();
+  // f of each row of T from ||t||^2 (unscaled in [2^-4, 2^12], else put in [4, 16))
+  const InstScale sc = InstScale::make(hsc.e(), band_exp(cg.rrn[0], kTLo, kTHi, kTTarget) >> 1,
+                                       band_exp(cg.rrn[1], kTLo, kTHi, kTTarget) >> 1);
+  if (sc.any()) {
+    const float s0 = pow2f(-sc.f(0)), s1 = pow2f(-sc.f(1));
+    scale_rows<NB>(cg.res, s0, s1);
+    scale_rows<NB>(cg.p, s0, s1);
+    cg.rrn[0] *= s0 * s0;
+    cg.rrn[1] *= s1 * s1;
   }
   __syncwarp();
   if constexpr (SOLVER == SOLVE_NEUMANN)
@@ -1196,7 +1606,8 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
 #pragma unroll
       for (int c = 0; c < 2; ++c) cg.p[hh][nt][c] = cg.v[hh][nt][c];
   float Er[NB][4], Ei[NB][4];
-  cg.matvec(frag, Er, Ei);
+  cg.matvec_s(frag, cg.es, Er, Ei);
+  const float sig = it.sigma * sc.s2();
   float qq[2] = {0.f, 0.f};
 #pragma unroll
   for (int hh = 0; hh < 2; ++hh)
@@ -1205,8 +1616,8 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const float2 vv = cg.v[hh][nt][c];
-        const float wx = fmaf(-it.sigma, vv.x, Er[nt][2 * hh + c]);
-        const float wy = fmaf(-it.sigma, vv.y, Ei[nt][2 * hh + c]);
+        const float wx = fmaf(-sig, vv.x, Er[nt][2 * hh + c]);
+        const float wy = fmaf(-sig, vv.y, Ei[nt][2 * hh + c]);
         qq[hh] = fmaf(vv.x, wx, fmaf(vv.y, wy, qq[hh]));
       }
   quad_sum2(qq[0], qq[1]);
@@ -1216,12 +1627,15 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
   for (int hh = 0; hh < 2; ++hh) {
     const int r = g + 8 * hh;
     const float nr = sqrtf(fmaxf(qq[hh], 0.f));
-    inv[hh] = it.normalize ? (nr > 0.f ? 1.f / nr : 0.f) : 1.f;
+    const float qs = sc.any() ? sc.xs(hh) : 1.f;
+    inv[hh] = it.normalize ? (nr > 0.f ? 1.f / nr : 0.f) : qs;
     if (r < it.R) {
-      if (t == 0 && it.qnorm) it.qnorm[r] = nr;
+      if (t == 0 && it.qnorm) it.qnorm[r] = nr * qs;
       if (cg.broke[hh]) flags |= ST_BREAKDOWN;
     }
   }
+  const float hsh = pow2f(-sc.e());  // H' = 2^-e H in the second pass too
+  const bool hscaled = sc.e() != 0;
 
   // ---- line 20: q = H v on the tensor cores, 8 antennas per n-tile
   uint32_t vh[NB][4], vl[NB][4];
@@ -1281,6 +1695,12 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
           e[ks][j] = (b < it.B && u < it.U) ? ldg2(it.H + b * it.U + u) : z;
         }
     }
+    if (hscaled) {
+#pragma unroll
+      for (int ks = 0; ks < NB; ++ks)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) e[ks][j] = make_float2(e[ks][j].x * hsh, e[ks][j].y * hsh);
+    }
     float qr[4] = {0.f, 0.f, 0.f, 0.f}, qi[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int ks = 0; ks < NB; ++ks) {
@@ -1328,19 +1748,32 @@ __device__ __forceinline__ void precode_warp_body(const Src& src, unsigned char*
   uint2* frag = reinterpret_cast<uint2*>(mine);
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
   int64_t cur = warp_first(src, int64_t(blockIdx.x) * (blockDim.x >> 5) + warp);
+  // An instance the fast path hands back (kRedo) runs once more with the
+  // scale of H taken from every entry (redo.w != 0).
+  InstScale redo;
+  redo.w = 0;
   while (cur >= 0) {
     const PreItem it = pre_item(src, cur);
     GramAcc<UT> Gr, Gi;
     VecAcc<UT> Mr, Mn;
+    InstScale sc = redo;
+    const bool again = redo.w != 0;
     int st;
     if (precode_vec<UT>(it)) {
-      warp_gram<UT, EL, X3, LD_VEC, false>(it.H, nullptr, it.B, it.U, 0, nullptr, Gr, Gi, Mr, Mn);
-      st = precode_warp_finish<UT, EL, X3, true, SOLVER>(it, frag, Gr, Gi);
+      warp_gram<UT, EL, X3, LD_VEC, false>(it.H, nullptr, it.B, it.U, 0, nullptr, Gr, Gi, Mr, Mn,
+                                           sc, again);
+      st = precode_warp_finish<UT, EL, X3, true, SOLVER>(it, frag, Gr, Gi, sc, !again);
     } else {
       warp_gram<UT, EL, X3, LD_ELEM, false>(it.H, nullptr, it.B, it.U, 0, nullptr, Gr, Gi, Mr,
-                                            Mn);
-      st = precode_warp_finish<UT, EL, X3, false, SOLVER>(it, frag, Gr, Gi);
+                                            Mn, sc, again);
+      st = precode_warp_finish<UT, EL, X3, false, SOLVER>(it, frag, Gr, Gi, sc, !again);
     }
+    if (st == kRedo) {
+      redo = full_scale<false>(it.H, nullptr, it.B, it.U, 0);
+      redo.w |= 1 << 25;  // marks the second pass even when every scale is 1
+      continue;
+    }
+    redo.w = 0;
     __syncwarp();
     if constexpr (SrcTraits<Src>::kDyn) {
       if ((threadIdx.x & 31) == 0) src_done(src, cur, st);

@@ -1,9 +1,10 @@
 // CG-D with the exact SINR tracker (Eq. 10) on the warp-per-instance
-// tensor-core bodies, for up to 16 users: the staging, Gram, matched filter,
+// tensor-core bodies, for up to 32 users: the staging, Gram, matched filter,
 // CG and LLRs of detect_warp_kernel, with the L_k recursion of every
-// right-hand side run as 16 x 16 tensor-core products (WarpCg::exact_sinr).
-// Three 16 x 16 complex L matrices live in registers, so these kernels are
-// built for 2 resident CTAs (8 warps) per SM.
+// right-hand side run as tensor-core products of 16 rows of L at a time
+// (WarpCg::exact_sinr; 32 users take two halves). Three 16-row complex L
+// blocks live in registers, so these kernels are built for 2 resident CTAs
+// (8 warps) per SM.
 #include <mutex>
 #include <unordered_map>
 
@@ -33,8 +34,9 @@ std::unordered_map<uint64_t, int> g_occ;  // (device, kernel id) -> resident CTA
 // when it is positive).
 template <typename Kern>
 cudaError_t grid_for(Kern kern, uint64_t id, int64_t n_work, int max_grid, int* grid) {
-  constexpr uint32_t smem = WarpCfg<16>::SMEM > WarpCfg<8>::SMEM ? WarpCfg<16>::SMEM
-                                                                  : WarpCfg<8>::SMEM;
+  constexpr uint32_t smem = WarpCfg<32>::SMEM;  // the largest slice (UT = 32)
+  static_assert(WarpCfg<32>::SMEM >= WarpCfg<16>::SMEM && WarpCfg<32>::SMEM >= WarpCfg<8>::SMEM,
+                "one attribute value serves every padded user count");
   DeviceInfo di;
   if (device_info(&di) != 0) return cudaErrorUnknown;
   int dev = 0;
@@ -110,6 +112,7 @@ cudaError_t launch_batch_warp_exact(int UT, int el, bool x3, const BatchArgs& b,
   switch (UT < 8 ? 8 : UT) {
     case 8: return batch_ut<8>(el, x3, b, max_grid, s, launch, grid_out);
     case 16: return batch_ut<16>(el, x3, b, max_grid, s, launch, grid_out);
+    case 32: return batch_ut<32>(el, x3, b, max_grid, s, launch, grid_out);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -119,6 +122,7 @@ cudaError_t launch_detect_warp_exact(int UT, int el, bool x3, const DetectArgs& 
   switch (UT < 8 ? 8 : UT) {
     case 8: return det_ut<8>(el, x3, a, s);
     case 16: return det_ut<16>(el, x3, a, s);
+    case 32: return det_ut<32>(el, x3, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -38,16 +38,10 @@ inline uint32_t serve_smem(const DeviceInfo& d, uint32_t need) {
 cudaError_t launch_detect(int UT, const DetectArgs& a, cudaStream_t s, int* grid_out);
 cudaError_t launch_precode(int UT, const PrecodeArgs& a, cudaStream_t s, int* grid_out);
 
-// Tensor-core variants (defined in tc.cu); el: 0 = BF16, 1 = FP16; x3: hi+lo split.
-cudaError_t launch_detect_tc(int UT, int el, bool x3, const DetectArgs& a, cudaStream_t s,
-                             int* grid_out);
-cudaError_t launch_precode_tc(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s,
-                              int* grid_out);
-uint32_t tc_detect_smem_bytes(int UT, int B, int U, int R, int exact);
-uint32_t tc_precode_smem_bytes(int UT, int B, int U, int R);
-
-// Batched tensor-core kernels (tc.cu): op 0 = detect, 1 = precode. With
-// launch = false only the launch shape is computed (smem bytes, grid).
+// Batched problems (tc.cu): op 0 = detect, 1 = precode; one bin of the
+// warp-per-instance kernels, with the exact tracker when b.PEX. With
+// launch = false only the launch shape is computed (grid). el: 0 = BF16,
+// 1 = FP16; x3: hi+lo split; full is unused (kept by the bin keys).
 cudaError_t launch_batch_tc(int op, int UT, int el, bool x3, bool full, const BatchArgs& b,
                             int max_grid, cudaStream_t s, bool launch, uint32_t* smem_out,
                             int* grid_out);
@@ -66,14 +60,11 @@ cudaError_t launch_neumann_detect(int UT, int el, bool x3, const DetectArgs& a, 
 cudaError_t launch_neumann_precode(int UT, int el, bool x3, const PrecodeArgs& a, cudaStream_t s);
 cudaError_t launch_batch_warp(int op, int UT, int el, bool x3, const BatchArgs& b, int max_grid,
                               cudaStream_t s, bool launch, int* grid_out);
-// Serving kernels (serve_kernels.cu): the warp kernel of the six
-// approximate-tracker classes and the CTA kernels of exact-tracker
-// detection. With launch = false only the resident CTAs are computed.
+// Serving kernel (serve_kernels.cu): the warp kernel of every class. With
+// launch = false only the resident CTAs are computed.
 struct ServeArgs;
 cudaError_t launch_serve_warp(int el, bool x3, const ServeArgs& sa, int grid, cudaStream_t s,
                               bool launch, int* resident_out);
-cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
-                            cudaStream_t st, bool launch, int* resident_out);
 
 // Implicit-product FP32 kernels (implicit.cu): e = H^H (H p) + sigma p; with
 // cgls = true, CG least squares on the augmented systems (Sec. III-E).

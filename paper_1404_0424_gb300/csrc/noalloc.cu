@@ -16,9 +16,9 @@ namespace {
 constexpr size_t kDescBytes = sizeof(cg_desc) * CG_STATIC_MAX_PROBLEMS;
 constexpr size_t kWorkOff = (kDescBytes + 255) & ~size_t(255);
 constexpr size_t kWorkBytes = sizeof(int2) * CG_STATIC_MAX_INSTANCES;
-// 2 operations x 3 padded user counts x FULL or not, plus exact-tracker
-// detection with 8 or 16 padded users x FULL or not
-constexpr int kMaxBins = 16;
+// 2 operations x 3 padded user counts x FULL or not, then exact-tracker
+// detection with 8, 16 or 32 padded users x FULL or not
+constexpr int kMaxBins = 18;
 constexpr size_t kCountOff = (kWorkOff + kWorkBytes + 255) & ~size_t(255);
 constexpr size_t kScratchBytes = kCountOff + sizeof(unsigned long long) * kMaxBins;
 static_assert(kScratchBytes <= (size_t(1) << 20), "static scratch stays within 1 MiB");
@@ -28,21 +28,17 @@ static_assert(kScratchBytes <= (size_t(1) << 20), "static scratch stays within 1
 // holds it until the process exits.
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
-std::mutex g_mu;                        // serialises the host side of calls
-void* g_addr[64] = {nullptr};           // device address of the scratch, per device
+std::mutex g_mu;                            // serialises the host side of calls
 int2 g_host_work[CG_STATIC_MAX_INSTANCES];  // host staging of the work units
 
-// Device address of the scratch on the current device; resolved once per
-// device, with that device current.
-int scratch_address(int dev, unsigned char** out) {
-  if (dev < 0 || dev >= 64) return CG_ECUDA;
-  if (g_addr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr)
-      return CG_ECUDA;
-    g_addr[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_addr[dev]);
+// Device address of the scratch on the current device. It is looked up on
+// every call: once the module is loaded this is a table lookup, and a
+// cached address would go stale if the device's context were torn down and
+// the module loaded again elsewhere (cudaDeviceReset).
+int scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) return CG_ECUDA;
+  *out = static_cast<unsigned char*>(p);
   return CG_OK;
 }
 
@@ -70,12 +66,15 @@ struct StaticBin {
   int64_t count, off;
 };
 
+// Bin of a problem: (operation, padded users, FULL) for the approximate
+// tracker and precoding, and bins of their own for exact-tracker detection,
+// as cg_plan_create keys them, so that an exact problem never moves the
+// approximate ones of its padded user count onto another kernel.
 int bin_of(const cg_desc& d, int* UT, int* full) {
   *UT = padded_users(d.U) < 8 ? 8 : padded_users(d.U);
   *full = (d.U == *UT && d.B % 8 == 0) ? 1 : 0;
   const int uti = *UT == 8 ? 0 : *UT == 16 ? 1 : 2;
-  if (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT && uti < 2)
-    return 12 + uti * 2 + *full;
+  if (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT) return 12 + uti * 2 + *full;
   return (d.op * 3 + uti) * 2 + *full;
 }
 
@@ -95,16 +94,17 @@ extern "C" int cg_batch_run_static(const cg_desc* descs, int64_t n, int32_t prec
   }
   if (units == 0) return CG_OK;
   std::lock_guard<std::mutex> lk(g_mu);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return CG_ECUDA;
   unsigned char* base = nullptr;
-  int rc = scratch_address(dev, &base);
+  int rc = scratch_address(&base);
   if (rc != CG_OK) return rc;
 
-  // bins: count, offsets, then fill the host staging of the work units
+  // bins: count, offsets, then fill the host staging of the work units;
+  // problems without instances take no part (they size no bin)
   StaticBin bins[kMaxBins];
-  for (int b = 0; b < kMaxBins; ++b) bins[b] = StaticBin{b < 12 ? b / 6 : 0, 0, b & 1, 0, 0, 0, 0, 0};
+  for (int b = 0; b < kMaxBins; ++b)
+    bins[b] = StaticBin{b < 12 ? b / 6 : CG_OP_DETECT, 0, b & 1, 0, 0, 0, 0, 0};
   for (int64_t i = 0; i < n; ++i) {
+    if (descs[i].n_inst == 0) continue;
     int UT, full;
     StaticBin& b = bins[bin_of(descs[i], &UT, &full)];
     b.UT = UT;
@@ -112,6 +112,20 @@ extern "C" int cg_batch_run_static(const cg_desc* descs, int64_t n, int32_t prec
     b.PR = b.PR > descs[i].R ? b.PR : descs[i].R;
     if (descs[i].op == CG_OP_DETECT && descs[i].sinr_mode == CG_SINR_EXACT) b.PEX = 1;
     b.count += descs[i].n_inst;
+  }
+  const int el = (precision == CG_PREC_BF16 || precision == CG_PREC_BF16X3) ? 0 : 1;
+  const bool x3 = precision == CG_PREC_BF16X3 || precision == CG_PREC_FP16X3;
+  // every bin's launch shape is checked before anything is enqueued
+  for (int b = 0; b < kMaxBins; ++b) {
+    if (bins[b].count == 0) continue;
+    BatchArgs a{};
+    a.n_work = bins[b].count;
+    a.PB = bins[b].PB;
+    a.PR = bins[b].PR;
+    a.PEX = bins[b].PEX;
+    const cudaError_t err = launch_batch_tc(bins[b].op, bins[b].UT, el, x3, bins[b].full != 0,
+                                            a, 0, nullptr, false, nullptr, nullptr);
+    if (err != cudaSuccess) return err == cudaErrorInvalidValue ? CG_EINVAL : CG_ECUDA;
   }
   int64_t off = 0;
   for (int b = 0; b < kMaxBins; ++b) {
@@ -138,8 +152,6 @@ extern "C" int cg_batch_run_static(const cg_desc* descs, int64_t n, int32_t prec
                       s) != cudaSuccess ||
       cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * kMaxBins, s) != cudaSuccess)
     return CG_ECUDA;
-  const int el = (precision == CG_PREC_BF16 || precision == CG_PREC_BF16X3) ? 0 : 1;
-  const bool x3 = precision == CG_PREC_BF16X3 || precision == CG_PREC_FP16X3;
   for (int b = 0; b < kMaxBins; ++b) {
     if (bins[b].count == 0) continue;
     BatchArgs a{};

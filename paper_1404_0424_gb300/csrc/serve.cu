@@ -1,9 +1,8 @@
 // Host side of the serving loop behind cg_serve_*: slots from a free list,
 // admission by HBM budget, publication through mapped host memory with no
 // CUDA call (a submit is a few stores and a release fence), on-demand launch
-// of the two persistent serving kernels (one for the six approximate-tracker
-// classes, one for exact-tracker detection; liveness read from mapped
-// memory), completion polling and bounded shutdown.
+// of the persistent serving kernel (liveness read from mapped memory),
+// completion polling and bounded shutdown.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -25,18 +24,16 @@ using namespace cgm;
 
 namespace {
 
-// (detect, precode) x (UT 8, 16, 32) and exact-tracker detection with 8 or 16
-// padded users on the warp-per-instance serving kernel (classes 0-7), and
-// exact-tracker detection with 32 padded users on the CTA kernel (class 8)
-constexpr int kClasses = 9;
-constexpr int kExactClass = 8;
+// (detect, precode) x (UT 8, 16, 32) and exact-tracker detection with 8, 16
+// or 32 padded users, all on the warp-per-instance serving kernel
+constexpr int kClasses = kWarpClasses;
 static_assert(kClasses <= kServeMaxClasses, "class count of the control block");
 constexpr int kRingPerSlot = 4;   // class ring positions per slot (ring = 4 x capacity)
-// Serving kernels: 0 serves classes 0-5, 1 the exact class. A kernel's
-// liveness counters in the control block are those of its ServeArgs::cls.
-constexpr int kKernels = 2;
-int kernel_of(int cls) { return cls == kExactClass ? 1 : 0; }
-int live_index(int k) { return k == 0 ? 0 : kExactClass; }
+// One serving kernel; its liveness counters in the control block are those
+// of its ServeArgs::cls.
+constexpr int kKernels = 1;
+int kernel_of(int) { return 0; }
+int live_index(int) { return 0; }
 
 int64_t mono_ns() {
   timespec ts;
@@ -45,18 +42,14 @@ int64_t mono_ns() {
 }
 
 // Class of a request: (operation, padded users 8 / 16 / 32), one warp per
-// instance; detection with the exact tracker (Eq. 10) has classes 6 and 7 on
-// the warp kernel up to 16 users (as single calls and plans) and class 8 on
-// the CTA kernel, whose shared memory holds the 32 x 32 recursion.
+// instance; detection with the exact tracker (Eq. 10) has classes 6, 7, 8
+// for 8, 16, 32 padded users (the kernels of single calls and plans).
 int class_of(const cg_desc& d, int* UT) {
   const int pu = padded_users(d.U);
   *UT = pu < 8 ? 8 : pu;
-  if (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT) {
-    if (*UT <= 16) return *UT == 8 ? 6 : 7;
-    *UT = 32;
-    return kExactClass;
-  }
-  return d.op * 3 + (*UT == 8 ? 0 : *UT == 16 ? 1 : 2);
+  const int uti = *UT == 8 ? 0 : *UT == 16 ? 1 : 2;
+  if (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT) return 6 + uti;
+  return d.op * 3 + uti;
 }
 
 
@@ -128,7 +121,7 @@ ServeArgs args_for(const cg_server* s, int k) {
   a.cap = s->ring;
   a.PB = s->cfg.max_B;
   a.PR = s->cfg.max_R;
-  a.PEX = k == 1 ? 1 : 0;
+  a.PEX = 0;
   a.poll_host = 1;
   a.idle_ns = (unsigned long long)s->cfg.idle_timeout_ms * 1000000ull;
   a.gen = s->launched_gen[k];
@@ -138,9 +131,7 @@ ServeArgs args_for(const cg_server* s, int k) {
 // Launches serving kernel k (or, with launch = false, reports its resident CTAs).
 cudaError_t launch_kernel(const cg_server* s, int k, bool launch, int* resident) {
   const ServeArgs a = args_for(s, k);
-  if (k == 0) return launch_serve_warp(s->el, s->x3, a, s->grid[0], s->ks[0], launch, resident);
-  return launch_serve_tc(CG_OP_DETECT, 32, s->el, s->x3, a, s->grid[1], s->ks[1], launch,
-                         resident);
+  return launch_serve_warp(s->el, s->x3, a, s->grid[k], s->ks[k], launch, resident);
 }
 
 // Launches the serving kernel of a class unless a launch of it is still
@@ -265,18 +256,13 @@ int cg_serve_create(const cg_serve_cfg* cfg, cg_server** out) {
     rc = CG_ECUDA;
   for (int k = 0; k < kKernels && rc == CG_OK; ++k)
     if (cudaStreamCreateWithFlags(&s->ks[k], cudaStreamNonBlocking) != cudaSuccess) rc = CG_ECUDA;
-  // launch shapes: every serving CTA fills one SM (its shared memory is
-  // padded past half an SM). The exact-tracker kernel has 1/16 of the SMs and
-  // the warp kernel the rest, so either one, relaunched while the other runs,
-  // finds SMs free for all of its CTAs.
+  // launch shape: every serving CTA fills one SM (its shared memory is
+  // padded past half an SM), one CTA on every SM
   DeviceInfo di;
   if (rc == CG_OK && device_info(&di) != 0) rc = CG_ECUDA;
   if (rc == CG_OK) {
-    const int exact = std::max(1, di.sm_count / 16);
-    s->grid[1] = exact;
-    s->grid[0] = di.sm_count - exact;
-    if (c.ctas_per_class > 0)
-      for (int k = 0; k < kKernels; ++k) s->grid[k] = std::min(s->grid[k], c.ctas_per_class);
+    s->grid[0] = di.sm_count;
+    if (c.ctas_per_class > 0) s->grid[0] = std::min(s->grid[0], c.ctas_per_class);
   }
   for (int k = 0; k < kKernels && rc == CG_OK; ++k) {
     int resident = 0;

@@ -1,6 +1,5 @@
-// Launchers of the serving kernels: the warp kernel of the six
-// approximate-tracker classes and the CTA kernels of exact-tracker
-// detection. Every serving CTA is padded to one per SM (serve_smem).
+// Launcher of the serving kernel, the warp-per-instance kernel of every
+// class. Every serving CTA is padded to one per SM (serve_smem).
 #include <mutex>
 #include <unordered_map>
 
@@ -67,39 +66,6 @@ cudaError_t warp_serve(const ServeArgs& sa, int grid, cudaStream_t s, bool launc
   return cudaGetLastError();
 }
 
-template <int UT, int EL, bool X3>
-cudaError_t cta_serve(int op, const ServeArgs& s, int grid, cudaStream_t st, bool launch,
-                      int* resident_out) {
-  constexpr int NTHR = TcCfg<UT>::NTHR;
-  DeviceInfo di;
-  if (device_info(&di) != 0) return cudaErrorUnknown;
-  // padded to one CTA per SM like every serving CTA
-  const uint32_t smem = serve_smem(di, op == 0 ? tc_detect_plan<UT>(s.PB, UT, s.PR, s.PEX).total
-                                               : tc_precode_plan<UT>(s.PB, UT, s.PR).total);
-  int res = 0;
-  const uint64_t id = (op == 0 ? 0x100 : 0x200) | (UT << 2) | (EL << 1) | (X3 ? 1 : 0);
-  cudaError_t err = op == 0 ? resident(detect_tc_serve_kernel<UT, EL, X3>, id, NTHR, smem, &res)
-                            : resident(precode_tc_serve_kernel<UT, EL, X3>, id, NTHR, smem, &res);
-  if (err != cudaSuccess) return err;
-  if (resident_out) *resident_out = res;
-  if (!launch) return cudaSuccess;
-  if (op == 0)
-    detect_tc_serve_kernel<UT, EL, X3><<<unsigned(grid), NTHR, smem, st>>>(s);
-  else
-    precode_tc_serve_kernel<UT, EL, X3><<<unsigned(grid), NTHR, smem, st>>>(s);
-  return cudaGetLastError();
-}
-
-template <int UT>
-cudaError_t cta_serve_ut(int op, int el, bool x3, const ServeArgs& s, int grid, cudaStream_t st,
-                         bool l, int* res) {
-  if (el == EL_BF16)
-    return x3 ? cta_serve<UT, EL_BF16, true>(op, s, grid, st, l, res)
-              : cta_serve<UT, EL_BF16, false>(op, s, grid, st, l, res);
-  return x3 ? cta_serve<UT, EL_F16, true>(op, s, grid, st, l, res)
-            : cta_serve<UT, EL_F16, false>(op, s, grid, st, l, res);
-}
-
 }  // namespace
 
 cudaError_t launch_serve_warp(int el, bool x3, const ServeArgs& sa, int grid, cudaStream_t s,
@@ -109,16 +75,6 @@ cudaError_t launch_serve_warp(int el, bool x3, const ServeArgs& sa, int grid, cu
               : warp_serve<EL_BF16, false>(sa, grid, s, launch, resident_out);
   return x3 ? warp_serve<EL_F16, true>(sa, grid, s, launch, resident_out)
             : warp_serve<EL_F16, false>(sa, grid, s, launch, resident_out);
-}
-
-cudaError_t launch_serve_tc(int op, int UT, int el, bool x3, const ServeArgs& s, int grid,
-                            cudaStream_t st, bool launch, int* resident_out) {
-  switch (UT) {
-    case 8: return cta_serve_ut<8>(op, el, x3, s, grid, st, launch, resident_out);
-    case 16: return cta_serve_ut<16>(op, el, x3, s, grid, st, launch, resident_out);
-    case 32: return cta_serve_ut<32>(op, el, x3, s, grid, st, launch, resident_out);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 }  // namespace cgm

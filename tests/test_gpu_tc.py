@@ -85,10 +85,14 @@ def test_detect_exact_tracker_at_K_equals_U(cabi, mode, B, U):
 @pytest.mark.parametrize("mode", list(X3))
 @pytest.mark.parametrize("B,U,R,K", [(32, 4, 3, 1), (32, 4, 3, 2), (128, 16, 14, 3),
                                      (64, 8, 5, 8), (96, 12, 4, 5), (128, 16, 16, 16),
-                                     (5, 3, 2, 2), (64, 13, 16, 5), (128, 16, 9, 4)])
+                                     (5, 3, 2, 2), (64, 13, 16, 5), (128, 16, 9, 4),
+                                     (256, 32, 14, 8), (128, 32, 5, 3), (64, 32, 16, 12),
+                                     (100, 17, 3, 6), (48, 24, 7, 24), (256, 32, 2, 32),
+                                     (40, 32, 1, 1)])
 def test_detect_exact_tracker_warp_kernel(cabi, mode, B, U, R, K):
-    # up to 16 users the exact tracker (Eq. 10) runs in the warp kernel, its
-    # L_k recursion as 16 x 16 tensor-core products; 8 dB keeps mu away from 1
+    # the exact tracker (Eq. 10) runs in the warp kernel, its L_k recursion
+    # as tensor-core products of 16 rows of L at a time (two halves at more
+    # than 16 users); 8 dB keeps mu away from 1
     d = wl.uplink(B, U, 6, n=4, R=R, snr_db=8.0, seed=11 * B + U + K)
     check_detect(run(cabi, d, K, X3[mode], "exact"),
                  oracle.cg_detect(d["H"], d["Y"], d["N0"], 1.0, K, 6, "exact"))
