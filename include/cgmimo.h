@@ -64,7 +64,8 @@ extern "C" {
 /* Per-instance status bits. */
 #define CG_STATUS_BREAKDOWN 1  /* CG stopped before K: ||r_{k-1}||^2 or Re(p^H A p) not > 0 */
 #define CG_STATUS_MU_NONPOS 2  /* some mu_{i|K} <= 0: that user's LLRs are set to 0 */
-#define CG_STATUS_TIMEOUT 4    /* an input copy did not complete in time; outputs not written */
+#define CG_STATUS_TIMEOUT 4    /* an input copy did not complete in time (FP32 kernels,
+                                  cg_set_wait_limit); outputs not written */
 
 /* SINR tracker (Sec. III-C). */
 #define CG_SINR_APPROX 0  /* Eqs. 11-13: diagonal recursion, rho = G_ii / N0 */
@@ -211,24 +212,29 @@ typedef struct cg_desc {
   int32_t* status;
 } cg_desc;
 
-/* Precision value for plans: let the autotuner pick among the modes that
- * meet FP32-level accuracy (CG_PREC_FP32, CG_PREC_FP16X3, CG_PREC_BF16X3). */
+/* Precision value for plans: let the autotuner pick the schedule and the
+ * split precision (CG_PREC_FP16X3 or CG_PREC_BF16X3, both FP32-accurate). */
 #define CG_PREC_AUTO (-1)
 
 typedef struct cg_plan cg_plan;
 
 /* Builds a plan for n problems (descs is a HOST array; the library keeps a
  * device copy, so the descriptor memory may be reused after the call).
- * Problems are grouped into bins by operation and padded user count; each
- * bin runs one persistent fused kernel whose CTAs claim (problem, instance)
- * work units from a device counter, so uneven problems balance across SMs.
- * All bins are captured once into a CUDA graph on `stream` and replayed by
- * cg_plan_run. precision is a CG_PREC_* value or CG_PREC_AUTO, which times
- * the candidates on the batch itself (the plan's first run is then done;
- * results are cached per device and shape class). The plan owns its device
- * memory until cg_plan_destroy. The buffers named by the descriptors must
- * stay valid while the plan is used. Returns CG_EINVAL for an invalid
- * descriptor (the first bad index is reported in *bad_index if non-NULL). */
+ * Problems are grouped into bins by operation, padded user count and
+ * tracker; each bin runs one persistent fused kernel whose warps claim
+ * (problem, instance) work units from a device counter, so uneven problems
+ * balance across SMs. All bins are captured once into a CUDA graph and
+ * replayed by cg_plan_run; creation is ordered after earlier work on
+ * `stream`. precision is a CG_PREC_* tensor-core value (the default
+ * schedule: longest units first, bins side by side, full grids) or
+ * CG_PREC_AUTO, for which the schedule autotuner times its candidates on
+ * the batch itself (claim order, bins side by side or one after another,
+ * grid share, split precision; these runs write the outputs) and keeps the
+ * fastest per device and shape class for later plans (cg_tune_cache_*).
+ * The plan owns its device memory until cg_plan_destroy. The buffers named
+ * by the descriptors must stay valid while the plan is used. Returns
+ * CG_EINVAL for an invalid descriptor (the first bad index is reported in
+ * *bad_index if non-NULL). */
 int cg_plan_create(const cg_desc* descs, int64_t n, int32_t precision, void* stream,
                    cg_plan** plan, int64_t* bad_index);
 
@@ -238,8 +244,38 @@ int cg_plan_run(cg_plan* plan, void* stream);
 /* Precision chosen for the plan (after autotuning) and the number of bins. */
 int cg_plan_info(const cg_plan* plan, int32_t* precision, int32_t* n_bins);
 
+/* How a plan runs its bins (cg_plan_schedule). */
+#define CG_TUNE_FIXED 0   /* precision given: the default schedule */
+#define CG_TUNE_TIMED 1   /* CG_PREC_AUTO: timed on this batch now */
+#define CG_TUNE_CACHED 2  /* CG_PREC_AUTO: taken from the autotuner's cache */
+typedef struct cg_schedule {
+  int32_t precision;   /* CG_PREC_* the plan runs */
+  int32_t order;       /* 0: work units claimed in descriptor order; 1: longest first */
+  int32_t concurrent;  /* 1: bins side by side on forked streams; 0: one after another */
+  int32_t grid_pct;    /* grid of each bin, in percent of its resident CTAs */
+  int32_t source;      /* CG_TUNE_* */
+  float ms;            /* one run as the autotuner timed it (0 if not timed) */
+} cg_schedule;
+
+/* The schedule the plan runs. */
+int cg_plan_schedule(const cg_plan* plan, cg_schedule* out);
+
 /* Releases the plan (waits for its outstanding runs first). */
 int cg_plan_destroy(cg_plan* plan);
+
+/* The autotuner's cache of schedules, keyed by device name and shape class.
+ * It lives in host memory; cg_tune_cache_save writes it to a JSON file (an
+ * array with one object per entry, one entry per line: key, precision,
+ * order, concurrent, grid_pct, ms) and cg_tune_cache_load merges a file
+ * written that way (so a schedule tuned on one machine can be shipped to
+ * others with the same device). If the environment variable
+ * CGMIMO_TUNE_CACHE names a file, the first plan that needs the cache loads
+ * it and every new entry rewrites it. load returns the number of entries
+ * read, save the number written, or CG_EINVAL (unreadable or malformed
+ * file: nothing merged). Host-only: no CUDA call. */
+int cg_tune_cache_load(const char* path);
+int cg_tune_cache_save(const char* path);
+int cg_tune_cache_size(void);
 
 /* ------------------------------------------------------------------------
  * Serving: a device-resident request loop with continuous batching
@@ -367,6 +403,19 @@ int cg_serve_destroy(cg_server* s);
  * Calls whose work overlaps on the GPU (different streams, or other
  * threads) race on the array: order them on one stream. */
 int cg_batch_run_static(const cg_desc* descs, int64_t n, int32_t precision, void* stream);
+
+/* Limit on the device-side wait of the FP32 kernels (CG_PREC_FP32, and the
+ * implicit and CGLS modes) for an instance's inputs, which they fetch with
+ * bulk copies into shared memory: after timeout_ns nanoseconds of GPU time
+ * without the copies landing, the instance's status gets CG_STATUS_TIMEOUT,
+ * its CTA waits (at most 2 s) for the copies still in flight and stops, and
+ * the call completes without a fault; the remaining instances of that CTA
+ * are left unwritten. 0 restores the default of 2 s; the limit applies to
+ * calls made after it is set, in every thread. The paper has no counterpart:
+ * it exists so that the timeout path can be exercised. Returns CG_EINVAL
+ * outside [0, 60 s]. The tensor-core kernels stage their inputs with copies
+ * that always complete and have no such wait. */
+int cg_set_wait_limit(int64_t timeout_ns);
 
 /* Frees the workspace of the *_host calls on the current device. */
 int cg_release_workspace(void);

@@ -98,6 +98,11 @@ _SIGS = {
     "cg_serve_poll": [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
                       ctypes.POINTER(CgReqStats)],
     "cg_serve_destroy": [_VP],
+    "cg_set_wait_limit": [ctypes.c_int64],
+    "cg_plan_schedule": [_VP, _VP],
+    "cg_tune_cache_load": [ctypes.c_char_p],
+    "cg_tune_cache_save": [ctypes.c_char_p],
+    "cg_tune_cache_size": [],
     "cg_strerror": [ctypes.c_int],
     "cg_version": [],
 }
@@ -152,6 +157,10 @@ def params(B, U, qam_bits, K, R, N0, Es=1.0, sinr_mode=0, amul_mode=0, precision
 
 def cg_strerror(code: int) -> str:
     return library().cg_strerror(int(code)).decode()
+
+
+def cg_set_wait_limit(timeout_ns: int) -> int:
+    return library().cg_set_wait_limit(int(timeout_ns))
 
 
 def cg_version() -> int:
@@ -218,6 +227,31 @@ def cg_plan_info(plan):
     nb = ctypes.c_int32()
     rc = library().cg_plan_info(plan, ctypes.byref(prec), ctypes.byref(nb))
     return rc, prec.value, nb.value
+
+
+class CgSchedule(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("concurrent", ctypes.c_int32), ("grid_pct", ctypes.c_int32),
+                ("source", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+def cg_plan_schedule(plan):
+    """Returns (rc, dict of the plan's schedule)."""
+    s = CgSchedule()
+    rc = library().cg_plan_schedule(plan, ctypes.byref(s))
+    return rc, {f: getattr(s, f) for f, _ in CgSchedule._fields_}
+
+
+def cg_tune_cache_load(path: str) -> int:
+    return library().cg_tune_cache_load(os.fsencode(path))
+
+
+def cg_tune_cache_save(path: str) -> int:
+    return library().cg_tune_cache_save(os.fsencode(path))
+
+
+def cg_tune_cache_size() -> int:
+    return library().cg_tune_cache_size()
 
 
 def cg_plan_destroy(plan) -> int:

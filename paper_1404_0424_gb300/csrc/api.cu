@@ -2,6 +2,7 @@
 // and the chunked host-memory variants.
 #include <cmath>
 #include <cstdint>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -13,6 +14,8 @@ namespace cgm {
 
 namespace {
 std::mutex g_dev_mu;
+// Limit of the FP32 kernels' wait for an instance's bulk copies (ns).
+std::atomic<int64_t> g_wait_ns{int64_t(WAIT_TIMEOUT_NS)};
 DeviceInfo g_dev[64];
 bool g_dev_ok[64] = {false};
 }  // namespace
@@ -83,6 +86,7 @@ int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void*
   a.sigma = p->N0 / p->Es;
   a.exact = p->sinr_mode == CG_SINR_EXACT;
   a.bulk = (p->B % 2 == 0) && aligned(H, 16) && aligned(Y, 16);
+  a.wait_ns = uint64_t(g_wait_ns.load(std::memory_order_relaxed));
   cudaError_t err;
   if (p->amul_mode == CG_AMUL_CGLS) {
     err = launch_detect_implicit(padded_users(p->U), a, s, true);
@@ -119,6 +123,7 @@ int precode_device(const cg_params* p, int64_t n_inst, const void* H, const void
   a.normalize = normalize != 0;
   a.bulk_h = ((p->B * p->U) % 2 == 0) && aligned(H, 16);
   a.bulk_t = ((p->R * p->U) % 2 == 0) && aligned(T, 16);
+  a.wait_ns = uint64_t(g_wait_ns.load(std::memory_order_relaxed));
   cudaError_t err;
   if (p->amul_mode == CG_AMUL_CGLS) {
     err = launch_precode_implicit(padded_users(p->U), a, s, true);
@@ -211,6 +216,13 @@ cudaError_t d2h(void* dst, const void* src, size_t n, cudaStream_t s) {
 }  // namespace
 
 extern "C" {
+
+int cg_set_wait_limit(int64_t timeout_ns) {
+  if (timeout_ns < 0 || timeout_ns > int64_t(60) * 1000000000) return CG_EINVAL;
+  g_wait_ns.store(timeout_ns == 0 ? int64_t(WAIT_TIMEOUT_NS) : timeout_ns,
+                  std::memory_order_relaxed);
+  return CG_OK;
+}
 
 int cg_detect(const cg_params* p, int64_t n_inst, const void* H, const void* Y, void* xhat,
               float* mu, float* rho, float* llr, int32_t* status, void* stream) {

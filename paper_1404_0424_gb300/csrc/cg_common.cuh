@@ -72,16 +72,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for phase `parity` of `bar` to complete; gives up after timeout_ns
-// of global time and returns false.
+// of global time and returns false. try_wait may suspend the thread for a
+// while by itself, so limits under 1 us poll with the non-blocking
+// test_wait instead, which lets such a limit run out before the phase does.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint64_t timeout_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
+  const bool poll = timeout_ns < 1000;
   const uint64_t t0 = global_timer_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (poll ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
     if (global_timer_ns() - t0 > timeout_ns) return false;
-    __nanosleep(64);
+    if (!poll) __nanosleep(64);
   }
 }
 

@@ -352,7 +352,7 @@ __device__ __forceinline__ bool implicit_stage_detect(const DetectArgs& a, const
       fence_proxy_async_smem();
       issue_detect_copies(a, io, smem, bar, n);
     }
-    if (!wait_inputs(bar, *parity)) {
+    if (!wait_inputs(bar, *parity, a.wait_ns)) {
       if (threadIdx.x == 0 && a.status) a.status[n] = ST_TIMEOUT;
       mbar_wait_bounded(bar, *parity, WAIT_TIMEOUT_NS);
       return false;
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) precode_implicit_kernel(con
     if (!a.bulk_t)
       for (int e = tid; e < R * U; e += NTHR) sT[e] = a.T[n * R * U + e];
     if (bulk) {
-      if (!wait_inputs(bar, parity)) {
+      if (!wait_inputs(bar, parity, a.wait_ns)) {
         if (tid == 0 && a.status) a.status[n] = ST_TIMEOUT;
         mbar_wait_bounded(bar, parity, WAIT_TIMEOUT_NS);
         return;

@@ -42,6 +42,7 @@ struct DetectArgs {
   float N0, Es, sigma;
   int exact;  // CG_SINR_EXACT
   int bulk;   // inputs may be fetched with 1-D bulk copies
+  uint64_t wait_ns;  // limit of the wait for an instance's bulk copies (cg_set_wait_limit)
 };
 
 struct PrecodeArgs {
@@ -56,6 +57,7 @@ struct PrecodeArgs {
   int normalize;
   int bulk_h;  // H may be fetched with bulk copies
   int bulk_t;  // T may be fetched with bulk copies
+  uint64_t wait_ns;  // limit of the wait for an instance's bulk copies (cg_set_wait_limit)
 };
 
 // Byte offsets into dynamic shared memory; computed identically on host and
@@ -167,10 +169,12 @@ __device__ __forceinline__ void coop_load_detect(const DetectArgs& a, const Smem
   }
 }
 
-// Waits for the bulk copies of the current instance. Returns false (for the
-// whole CTA) if they did not land in time; the caller then stops.
-__device__ __forceinline__ bool wait_inputs(uint64_t* bar, uint32_t parity) {
-  const bool ok = mbar_wait_bounded(bar, parity, WAIT_TIMEOUT_NS);
+// Waits for the bulk copies of the current instance, at most wait_ns of
+// global time. Returns false (for the whole CTA) if they did not land in
+// time; the caller then reports CG_STATUS_TIMEOUT, waits (with the 2 s
+// bound) for the copies still in flight into its shared memory, and stops.
+__device__ __forceinline__ bool wait_inputs(uint64_t* bar, uint32_t parity, uint64_t wait_ns) {
+  const bool ok = mbar_wait_bounded(bar, parity, wait_ns);
   return !__syncthreads_or(!ok);
 }
 
@@ -606,7 +610,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) detect_kernel(const DetectA
   for (; n < a.n_inst; n += gridDim.x) {
     // ---- step 1: inputs of instance n in shared memory
     if (a.bulk) {
-      if (!wait_inputs(bar, parity)) {
+      if (!wait_inputs(bar, parity, a.wait_ns)) {
         if (tid == 0 && a.status) a.status[n] = ST_TIMEOUT;
         mbar_wait_bounded(bar, parity, WAIT_TIMEOUT_NS);  // let in-flight copies land
         return;
@@ -742,7 +746,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) precode_kernel(const Precod
     if (!a.bulk_t)
       for (int e = tid; e < R * U; e += NTHR) sT[e] = a.T[n * R * U + e];
     if (bulk) {
-      if (!wait_inputs(bar, parity)) {
+      if (!wait_inputs(bar, parity, a.wait_ns)) {
         if (tid == 0 && a.status) a.status[n] = ST_TIMEOUT;
         mbar_wait_bounded(bar, parity, WAIT_TIMEOUT_NS);
         return;

@@ -337,6 +337,7 @@ constexpr int kTTarget = 2;
 // FP16 split).
 constexpr float kColMsLo = 0.00390625f;
 constexpr float kGHi = 67108864.f;
+constexpr float kPreColMsHi = 16.f;  // CG-P: G'_ii / B at most this (precode_warp_finish)
 constexpr float kRLo = 1.f, kRHi = 67108864.f;
 
 // Fast-path scale from H's first k-step (h as from load_h_ks /
@@ -1580,7 +1581,12 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
   }
   float Gd[NB][2], gmax;
   cg.es = WarpCg<UT, EL>::setup_a(Gr, Gi, it.sigma * hsc.s2(), frag, cg.D, Gd, gmax);
-  if (check && !(gmax == 0.f || (gmax >= kColMsLo * float(it.B) && gmax <= kGHi))) return kRedo;
+  // the solution v ~ t / lambda(A') enters the FP16 split of the products
+  // with H, so the columns of H' must also stay near unit power: the
+  // strongest one's mean square at most kPreColMsHi
+  if (check && !(gmax == 0.f || (gmax >= kColMsLo * float(it.B) &&
+                                 gmax <= kPreColMsHi * float(it.B))))
+    return kRedo;
   cg.init();
   // f of each row of T from ||t||^2 (unscaled in [2^-4, 2^12], else put in [4, 16))
   const InstScale sc = InstScale::make(hsc.e(), band_exp(cg.rrn[0], kTLo, kTHi, kTTarget) >> 1,

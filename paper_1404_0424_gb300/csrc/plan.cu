@@ -1,11 +1,22 @@
-// Batched uneven problems: plans, bins, CUDA-graph capture and the precision
+// Batched uneven problems: plans, bins, CUDA-graph capture and the schedule
 // autotuner behind cg_plan_create / cg_plan_run.
+//
+// A plan groups its problems into bins by operation, padded user count and
+// tracker; each bin runs one persistent warp-per-instance kernel whose warps
+// claim (problem, instance) units from a device counter. A schedule fixes
+// how: the order in which units are claimed (as given, or longest first, so
+// that the long units start early and the short ones fill the tail), whether
+// the bins run side by side on forked streams or one after another, what
+// share of its resident CTAs each bin's grid takes, and (with CG_PREC_AUTO)
+// the split precision. The autotuner times the candidates on the batch
+// itself and keeps the fastest per device and shape class (tune.cu).
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -13,6 +24,7 @@
 #include "cgmimo.h"
 #include "host_checks.h"
 #include "launch.cuh"
+#include "tune.h"
 
 using namespace cgm;
 
@@ -22,17 +34,24 @@ struct Bin {
   int op = 0, UT = 0;
   bool full = false;
   int PB = 0, PR = 0, PEX = 0;
-  std::vector<int2> work;  // (descriptor, instance)
-  int64_t work_off = 0;    // offset of this bin's units in the device work array
-  int grid = 0;
+  std::vector<int2> work;   // (descriptor, instance), in descriptor order
+  std::vector<float> cost;  // estimated cost of each unit (work_cost)
+  int64_t work_off = 0;     // offset of this bin's units in the device work array
+  int full_grid = 0;        // resident CTAs, at most one per four units
+  int grid = 0;             // grid of the schedule in use
 };
 
-struct Tuned {
-  int32_t precision;
-};
-
-std::mutex g_tune_mu;
-std::map<std::string, Tuned> g_tune;  // (device, shape class) -> choice
+// Estimated cost of one work unit, in units of tensor-core work: the Gram
+// and matched filter over B antennas, K products A p on 16 right-hand-side
+// rows (times the exact tracker's recursion), and for precoding q = H v.
+float work_cost(const cg_desc& d, int UT) {
+  const float B = float(d.B), U = float(UT), R = float(d.R), K = float(d.K);
+  if (d.op == CG_OP_DETECT) {
+    const float exact = d.sinr_mode == CG_SINR_EXACT ? 1.f + R * U / 8.f : 1.f;
+    return B * U * (U / 2.f + R) + K * 16.f * U * U * exact;
+  }
+  return B * U * U / 2.f + K * 16.f * U * U + B * 16.f * U;
+}
 
 int precision_el(int32_t prec) { return (prec == CG_PREC_BF16 || prec == CG_PREC_BF16X3) ? 0 : 1; }
 bool precision_x3(int32_t prec) { return prec == CG_PREC_BF16X3 || prec == CG_PREC_FP16X3; }
@@ -56,17 +75,19 @@ int check_desc(const cg_desc& d) {
   return CG_EINVAL;
 }
 
-// A short description of the plan's shape class, the autotuner's cache key.
+// The autotuner's cache key: device name, then per bin its shape and the
+// power of two above its unit count.
 std::string shape_key(const std::vector<Bin>& bins, int dev) {
   char name[256] = {0};
   cudaDeviceProp prop;
-  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) std::snprintf(name, sizeof(name), "%s", prop.name);
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+    std::snprintf(name, sizeof(name), "%s", prop.name);
   std::string k = name;
+  char buf[96];
   for (const Bin& b : bins) {
-    char buf[96];
     const size_t units = b.work.size();
     int scale = 0;
-    while ((size_t(1) << scale) < units) ++scale;  // size class, powers of two
+    while ((size_t(1) << scale) < units) ++scale;
     std::snprintf(buf, sizeof(buf), "|%d,%d,%d,%d,%d,%d,%d", b.op, b.UT, int(b.full), b.PB, b.PR,
                   b.PEX, scale);
     k += buf;
@@ -74,11 +95,16 @@ std::string shape_key(const std::vector<Bin>& bins, int dev) {
   return k;
 }
 
+// Schedule of a plan that asks for a fixed precision: longest first, bins
+// side by side, full grids.
+TuneEntry default_schedule(int32_t precision) { return TuneEntry{precision, 1, 1, 100, 0.f}; }
+
 }  // namespace
 
 struct cg_plan {
   int dev = 0;
-  int32_t precision = CG_PREC_FP16X3;
+  TuneEntry sched{CG_PREC_FP16X3, 1, 1, 100, 0.f};
+  int32_t source = CG_TUNE_FIXED;
   std::vector<Bin> bins;
   void* dmem = nullptr;
   cg_desc* d_desc = nullptr;
@@ -89,6 +115,7 @@ struct cg_plan {
   std::vector<cudaEvent_t> ev;  // [0] fork, [1..] joins
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  std::vector<int2> staging;    // host copy of the ordered work units
 };
 
 namespace {
@@ -100,20 +127,46 @@ void release_graph(cg_plan* p) {
   p->graph = nullptr;
 }
 
-// Captures memset(counters) + one persistent kernel per bin (bins forked onto
-// side streams so they run concurrently) into p->graph / p->exec.
-int capture(cg_plan* p, int32_t precision) {
+// Uploads every bin's work units in the order of `s` and sets the bins'
+// grids; waits for the copy (the host staging is reused).
+int apply_order_and_grid(cg_plan* p, const TuneEntry& s) {
+  size_t units = 0;
+  for (const Bin& b : p->bins) units += b.work.size();
+  p->staging.resize(std::max<size_t>(units, 1));
+  for (Bin& b : p->bins) {
+    std::vector<size_t> idx(b.work.size());
+    std::iota(idx.begin(), idx.end(), size_t(0));
+    if (s.order == 1)
+      std::stable_sort(idx.begin(), idx.end(),
+                       [&](size_t x, size_t y) { return b.cost[x] > b.cost[y]; });
+    for (size_t i = 0; i < idx.size(); ++i) p->staging[size_t(b.work_off) + i] = b.work[idx[i]];
+    b.grid = std::max(1, int((int64_t(b.full_grid) * s.grid_pct + 99) / 100));
+  }
+  if (units == 0) return CG_OK;
+  if (cudaMemcpyAsync(p->d_work, p->staging.data(), sizeof(int2) * units, cudaMemcpyHostToDevice,
+                      p->capture) != cudaSuccess ||
+      cudaStreamSynchronize(p->capture) != cudaSuccess)
+    return CG_ECUDA;
+  return CG_OK;
+}
+
+// Captures memset(counters) + one persistent kernel per bin into p->graph /
+// p->exec: with s.concurrent the bins are forked onto side streams and run
+// side by side, otherwise one after another on the capture stream.
+int capture(cg_plan* p, const TuneEntry& s) {
   release_graph(p);
-  const int el = precision_el(precision);
-  const bool x3 = precision_x3(precision);
-  cudaStream_t s = p->capture;
-  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CG_ECUDA;
-  cudaError_t err = cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long) * p->bins.size(), s);
-  if (err == cudaSuccess) err = cudaEventRecord(p->ev[0], s);
+  const int el = precision_el(s.precision);
+  const bool x3 = precision_x3(s.precision);
+  cudaStream_t cs = p->capture;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CG_ECUDA;
+  cudaError_t err =
+      cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long) * p->bins.size(), cs);
+  if (err == cudaSuccess && s.concurrent) err = cudaEventRecord(p->ev[0], cs);
   for (size_t i = 0; i < p->bins.size() && err == cudaSuccess; ++i) {
     const Bin& b = p->bins[i];
-    cudaStream_t bs = i == 0 ? s : p->side[i - 1];
-    if (i > 0) err = cudaStreamWaitEvent(bs, p->ev[0], 0);
+    const bool fork = s.concurrent && i > 0;
+    cudaStream_t bs = fork ? p->side[i - 1] : cs;
+    if (fork) err = cudaStreamWaitEvent(bs, p->ev[0], 0);
     if (err != cudaSuccess) break;
     BatchArgs a{};
     a.desc = p->d_desc;
@@ -124,13 +177,13 @@ int capture(cg_plan* p, int32_t precision) {
     a.PR = b.PR;
     a.PEX = b.PEX;
     err = launch_batch_tc(b.op, b.UT, el, x3, b.full, a, b.grid, bs, true, nullptr, nullptr);
-    if (err == cudaSuccess && i > 0) {
+    if (err == cudaSuccess && fork) {
       err = cudaEventRecord(p->ev[i], bs);
-      if (err == cudaSuccess) err = cudaStreamWaitEvent(s, p->ev[i], 0);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(cs, p->ev[i], 0);
     }
   }
   cudaGraph_t g = nullptr;
-  const cudaError_t end = cudaStreamEndCapture(s, &g);
+  const cudaError_t end = cudaStreamEndCapture(cs, &g);
   if (err != cudaSuccess || end != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return err == cudaErrorInvalidValue ? CG_EINVAL : CG_ECUDA;
@@ -140,8 +193,13 @@ int capture(cg_plan* p, int32_t precision) {
     release_graph(p);
     return CG_ECUDA;
   }
-  p->precision = precision;
+  p->sched = s;
   return CG_OK;
+}
+
+int use_schedule(cg_plan* p, const TuneEntry& s) {
+  const int rc = apply_order_and_grid(p, s);
+  return rc != CG_OK ? rc : capture(p, s);
 }
 
 // Mean time of `reps` graph launches after one warm-up (milliseconds).
@@ -159,6 +217,36 @@ float time_graph(cg_plan* p, int reps) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   return ms / reps;
+}
+
+// The autotuner: every schedule candidate at FP16X3 (claim order x
+// concurrency x grid share), then BF16X3 at the best of them, which it
+// replaces only when it is at least 3% faster (FP16X3 keeps 22 significant
+// bits to BF16X3's 16). These runs write the plan's outputs.
+int autotune(cg_plan* p, TuneEntry* best) {
+  std::vector<TuneEntry> cands;
+  for (int order : {1, 0}) {
+    cands.push_back(TuneEntry{CG_PREC_FP16X3, order, 1, 100, 0.f});
+    if (p->bins.size() > 1) {
+      cands.push_back(TuneEntry{CG_PREC_FP16X3, order, 1, 50, 0.f});
+      cands.push_back(TuneEntry{CG_PREC_FP16X3, order, 0, 100, 0.f});
+    }
+  }
+  bool any = false;
+  for (TuneEntry c : cands) {
+    if (use_schedule(p, c) != CG_OK) continue;
+    c.ms = time_graph(p, 3);
+    if (!any || c.ms < best->ms) *best = c;
+    any = true;
+  }
+  if (!any) return CG_ECUDA;
+  TuneEntry bf = *best;
+  bf.precision = CG_PREC_BF16X3;
+  if (use_schedule(p, bf) == CG_OK) {
+    bf.ms = time_graph(p, 3);
+    if (bf.ms < 0.97f * best->ms) *best = bf;
+  }
+  return CG_OK;
 }
 
 void destroy_plan(cg_plan* p) {
@@ -199,7 +287,7 @@ int cg_plan_create(const cg_desc* descs, int64_t n, int32_t precision, void* str
   }
   // bins by (operation, padded users, FULL, exact tracker); each keeps its
   // largest B and R. Exact-tracker detection has bins of its own so that
-  // the other problems keep the warp-per-instance kernels.
+  // the other problems keep the approximate tracker's kernels.
   std::map<std::tuple<int, int, int, int>, size_t> index;
   for (int64_t i = 0; i < n; ++i) {
     const cg_desc& d = descs[i];
@@ -221,15 +309,19 @@ int cg_plan_create(const cg_desc* descs, int64_t n, int32_t precision, void* str
     Bin& b = p->bins[it->second];
     b.PB = std::max(b.PB, d.B);
     b.PR = std::max(b.PR, d.R);
-    if (d.op == CG_OP_DETECT && d.sinr_mode == CG_SINR_EXACT) b.PEX = 1;
-    for (int64_t k = 0; k < d.n_inst; ++k) b.work.push_back(make_int2(int(i), int(k)));
+    b.PEX |= exact;
+    const float c = work_cost(d, UT);
+    for (int64_t k = 0; k < d.n_inst; ++k) {
+      b.work.push_back(make_int2(int(i), int(k)));
+      b.cost.push_back(c);
+    }
   }
-  // device copy: descriptors, work units, one counter per bin
   size_t units = 0;
   for (Bin& b : p->bins) {
     b.work_off = int64_t(units);
     units += b.work.size();
   }
+  // device copy: descriptors, work units, one counter per bin
   const size_t bytes_desc = sizeof(cg_desc) * size_t(std::max<int64_t>(n, 1));
   const size_t off_work = (bytes_desc + 255) & ~size_t(255);
   const size_t off_cnt = (off_work + sizeof(int2) * std::max<size_t>(units, 1) + 255) & ~size_t(255);
@@ -255,23 +347,21 @@ int cg_plan_create(const cg_desc* descs, int64_t n, int32_t precision, void* str
     else p->ev.push_back(e);
   }
   if (rc == CG_OK && n > 0) {
-    // order after the caller's stream, upload, and wait (host vectors are temporary)
+    // order after the caller's stream, upload the descriptors and wait (the
+    // host array may be reused once the call returns)
     cudaEvent_t ready;
-    cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-    cudaEventRecord(ready, static_cast<cudaStream_t>(stream));
-    cudaStreamWaitEvent(p->capture, ready, 0);
-    if (cudaMemcpyAsync(p->d_desc, descs, sizeof(cg_desc) * size_t(n), cudaMemcpyHostToDevice,
-                        p->capture) != cudaSuccess)
-      rc = CG_ECUDA;
-    for (const Bin& b : p->bins)
-      if (rc == CG_OK && !b.work.empty() &&
-          cudaMemcpyAsync(p->d_work + b.work_off, b.work.data(), sizeof(int2) * b.work.size(),
-                          cudaMemcpyHostToDevice, p->capture) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) rc = CG_ECUDA;
+    if (rc == CG_OK) {
+      if (cudaEventRecord(ready, static_cast<cudaStream_t>(stream)) != cudaSuccess ||
+          cudaStreamWaitEvent(p->capture, ready, 0) != cudaSuccess ||
+          cudaMemcpyAsync(p->d_desc, descs, sizeof(cg_desc) * size_t(n), cudaMemcpyHostToDevice,
+                          p->capture) != cudaSuccess ||
+          cudaStreamSynchronize(p->capture) != cudaSuccess)
         rc = CG_ECUDA;
-    if (cudaStreamSynchronize(p->capture) != cudaSuccess && rc == CG_OK) rc = CG_ECUDA;
-    cudaEventDestroy(ready);
+      cudaEventDestroy(ready);
+    }
   }
-  // launch shapes (grid per bin: resident CTAs, at most one per work unit)
+  // full grids: resident CTAs of the bin's kernel, at most one per four units
   for (Bin& b : p->bins) {
     if (rc != CG_OK) break;
     BatchArgs a{};
@@ -281,39 +371,27 @@ int cg_plan_create(const cg_desc* descs, int64_t n, int32_t precision, void* str
     a.PEX = b.PEX;
     const int32_t prec = precision == CG_PREC_AUTO ? CG_PREC_FP16X3 : precision;
     const cudaError_t err = launch_batch_tc(b.op, b.UT, precision_el(prec), precision_x3(prec),
-                                            b.full, a, 0, nullptr, false, nullptr, &b.grid);
+                                            b.full, a, 0, nullptr, false, nullptr, &b.full_grid);
     if (err != cudaSuccess) rc = err == cudaErrorInvalidValue ? CG_EINVAL : CG_ECUDA;
   }
   if (rc == CG_OK && !p->bins.empty()) {
     if (precision != CG_PREC_AUTO) {
-      rc = capture(p, precision);
+      p->source = CG_TUNE_FIXED;
+      rc = use_schedule(p, default_schedule(precision));
     } else {
       const std::string key = shape_key(p->bins, p->dev);
-      int32_t chosen = -1;
-      {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune.find(key);
-        if (it != g_tune.end()) chosen = it->second.precision;
-      }
-      if (chosen < 0) {
-        // time the accurate candidates on this batch (these runs write the outputs)
-        float best = 1e30f;
-        const int32_t cands[2] = {CG_PREC_FP16X3, CG_PREC_BF16X3};
-        for (int32_t c : cands) {
-          if (capture(p, c) != CG_OK) continue;
-          const float ms = time_graph(p, 3);
-          if (ms < best) {
-            best = ms;
-            chosen = c;
-          }
-        }
-        if (chosen < 0) rc = CG_ECUDA;
-        else {
-          std::lock_guard<std::mutex> lk(g_tune_mu);
-          g_tune[key] = Tuned{chosen};
+      TuneEntry s{};
+      if (tune_lookup(key, &s)) {
+        p->source = CG_TUNE_CACHED;
+        rc = use_schedule(p, s);
+      } else {
+        rc = autotune(p, &s);
+        if (rc == CG_OK) {
+          tune_store(key, s);
+          p->source = CG_TUNE_TIMED;
+          rc = use_schedule(p, s);
         }
       }
-      if (rc == CG_OK) rc = capture(p, chosen);
     }
   }
   if (rc != CG_OK) {
@@ -335,8 +413,19 @@ int cg_plan_run(cg_plan* p, void* stream) {
 
 int cg_plan_info(const cg_plan* p, int32_t* precision, int32_t* n_bins) {
   if (p == nullptr) return CG_EINVAL;
-  if (precision) *precision = p->precision;
+  if (precision) *precision = p->sched.precision;
   if (n_bins) *n_bins = int32_t(p->bins.size());
+  return CG_OK;
+}
+
+int cg_plan_schedule(const cg_plan* p, cg_schedule* out) {
+  if (p == nullptr || out == nullptr) return CG_EINVAL;
+  out->precision = p->sched.precision;
+  out->order = p->sched.order;
+  out->concurrent = p->sched.concurrent;
+  out->grid_pct = p->sched.grid_pct;
+  out->source = p->source;
+  out->ms = p->sched.ms;
   return CG_OK;
 }
 

@@ -142,3 +142,9 @@ def test_cgls_and_neumann_reject_on_the_host(lib):
     assert lib.cg_neumann_detect(None, 1, None, None, None, None, None) == cabi.CG_EINVAL
     assert lib.cg_neumann_precode(None, 1, None, None, None, None, 0, None, None) == \
         cabi.CG_EINVAL
+
+
+def test_wait_limit_range(lib):
+    assert cabi.cg_set_wait_limit(-1) == cabi.CG_EINVAL
+    assert cabi.cg_set_wait_limit(61 * 10**9) == cabi.CG_EINVAL
+    assert cabi.cg_set_wait_limit(0) == cabi.CG_OK      # back to the 2 s default

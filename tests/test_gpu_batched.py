@@ -172,3 +172,49 @@ def test_auto_precision_and_config_batch(cabi):
             check_detect({k: to_np(v) for k, v in o.items()}, r)
     finally:
         cabi.cg_plan_destroy(plan)
+
+
+def test_autotuner_times_then_caches_schedules(cabi, tmp_path):
+    """CG_PREC_AUTO times the schedule candidates on the batch (source
+    TIMED); a second plan of the same shape class takes the schedule from the
+    cache (CACHED); the cache file round-trips through save and load; a fixed
+    precision gets the default schedule (FIXED). Every schedule gives the
+    single calls' results."""
+    dev = torch.device("cuda:0")
+    probs = make_batch(48, seed=21, dev=dev, exact_every=7)
+    ds = descs(cabi, probs)
+    rc, plan, bad = cabi.cg_plan_create(ds, -1)
+    assert rc == 0, (cabi.cg_strerror(rc), bad)
+    try:
+        rc, s1 = cabi.cg_plan_schedule(plan)
+        assert rc == 0 and s1["source"] == cabi.CG_TUNE_TIMED and s1["ms"] > 0
+        assert s1["precision"] in (3, 4) and s1["order"] in (0, 1) and 1 <= s1["grid_pct"] <= 100
+        assert cabi.cg_plan_run(plan) == 0
+        torch.cuda.synchronize()
+        for p in probs:
+            ref = single(cabi, p, s1["precision"])
+            torch.cuda.synchronize()
+            keys = ("xhat", "mu", "rho", "llr", "status") if p["op"] == 0 else ("q", "qnorm",
+                                                                               "status")
+            for k in keys:
+                assert torch.equal(p["t"][k], ref[k]), f"{k} differs from the single call"
+    finally:
+        cabi.cg_plan_destroy(plan)
+    rc, plan2, _ = cabi.cg_plan_create(ds, -1)
+    assert rc == 0
+    try:
+        rc, s2 = cabi.cg_plan_schedule(plan2)
+        assert s2["source"] == cabi.CG_TUNE_CACHED
+        assert all(s2[f] == s1[f] for f in ("precision", "order", "concurrent", "grid_pct"))
+    finally:
+        cabi.cg_plan_destroy(plan2)
+    path = tmp_path / "tune.json"
+    n = cabi.cg_tune_cache_save(str(path))
+    assert n >= 1 and cabi.cg_tune_cache_load(str(path)) == n
+    rc, plan3, _ = cabi.cg_plan_create(ds, 4)
+    assert rc == 0
+    try:
+        rc, s3 = cabi.cg_plan_schedule(plan3)
+        assert s3["source"] == cabi.CG_TUNE_FIXED and s3["precision"] == 4
+    finally:
+        cabi.cg_plan_destroy(plan3)
