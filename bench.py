@@ -3,14 +3,18 @@
 Workload (one step): S slots of the 128-antenna, 16-user, 64-QAM uplink and
 downlink, each slot 1200 subcarriers x 14 OFDM symbols with the channel
 constant over the 14 symbols (one instance = one subcarrier, 14 right-hand
-sides), i.i.d. CN(0,1) channels, SNR 10 dB, K = 3 CG iterations, FP32. A step
-is one cg_detect over all S*1200 instances (matched filter, Gram, CG,
+sides), i.i.d. CN(0,1) channels, SNR 10 dB, K = 3 CG iterations; by default
+the matched filter, Gram and q = H v run on the tensor cores with hi+lo split
+FP16 operands and FP32 accumulation, the CG recursion in FP32. A step is one
+cg_detect over all S*1200 instances (matched filter, Gram, CG,
 approximate SINR tracker, max-log LLRs) and one cg_precode over the same
 channels (Gram, CG, q = H v). Inputs are drawn once, resident in HBM and
 larger than L2.
 
-Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+Prints one JSON line (rank 0) on stdout with the headline figures, and the
+full record of every side measurement on stderr ("detail: {...}").
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload instead.
 """
 
 from __future__ import annotations
@@ -59,6 +63,10 @@ def parse():
 
 
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3, "fp16x3": 4}
+# arithmetic of each precision mode: tensor-core operands (x3 = hi+lo split,
+# three products) with FP32 accumulation, the CG recursion and LLRs in FP32
+DTYPES = {"fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32", "bf16x3": "bf16x3+f32",
+          "fp16x3": "f16x3+f32"}
 
 
 # ---------------------------------------------------------------------------
@@ -312,6 +320,7 @@ def run_batched(cabi, torch, dev, n_prob=4096, seed=2, reps=10):
     if rc:
         return {"error": cabi.cg_strerror(rc)}
     _, prec, nbins = cabi.cg_plan_info(plan)
+    _, sched = cabi.cg_plan_schedule(plan)
     for _ in range(3):
         cabi.cg_plan_run(plan, stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -332,11 +341,19 @@ def run_batched(cabi, torch, dev, n_prob=4096, seed=2, reps=10):
     torch.cuda.synchronize()
     ms_plain = e0.elapsed_time(e1)
     ok = all(int(o[4][0]) == 0 for _, _, o, *_ in keep)
+    peaks, kind = measured_peaks()
+    gbs = nbytes / (ms / 1e3) / 1e9
     return {"workload": "4096 uneven detection problems: (B,U) in {64x8,128x16,128x32,256x32}, "
                         "16/64/256-QAM, 1-14 symbols, SNR 5-25 dB, K=min(U/4,8)",
             "precision": {3: "bf16x3", 4: "fp16x3"}.get(prec, prec), "bins": nbins,
             "ms_per_run": round(ms, 4), "solves_per_s": round(solves / (ms / 1e3), 1),
-            "gb_per_s": round(nbytes / (ms / 1e3) / 1e9, 1),
+            "gb_per_s": round(gbs, 1), "frac_hbm": round(gbs / peaks["hbm_gbs"], 4),
+            "peak_kind": kind,
+            "schedule": {"order": ("given", "longest_first")[sched["order"]],
+                         "bins": ("sequential", "concurrent")[sched["concurrent"]],
+                         "grid_pct": sched["grid_pct"],
+                         "source": ("fixed", "timed", "cached")[sched["source"]],
+                         "tuned_ms": round(sched["ms"], 4)},
             "plain_one_launch_per_problem": {"ms": round(ms_plain, 3),
                                              "solves_per_s": round(solves / (ms_plain / 1e3), 1)},
             "status_ok": ok}
@@ -414,21 +431,34 @@ def run_large(cabi, torch, dev, precision):
 
 def run_serving(seconds):
     """Poisson arrivals at 20k requests/s (the load generator's mix), served
-    (cg_serve_*, FP16X3) and plain (one FP32 launch per request)."""
+    (cg_serve_*, FP16X3) and plain (one FP32 launch per request); then the
+    same mix at 500 and 5000 requests/s, where latency rather than
+    throughput is what a serving path has to show."""
     from paper_1404_0424_gb300 import build as bld
-    out = {}
-    for mode in ("served", "plain"):
-        cmd = [bld.LOADGEN, "--mode", mode, "--rate", "20000", "--seconds", str(seconds),
+
+    def one(mode, rate):
+        cmd = [bld.LOADGEN, "--mode", mode, "--rate", str(rate), "--seconds", str(seconds),
                "--capacity", "64", "--precision", "4", "--seed", "1"]
         try:
             res = subprocess.run(cmd, capture_output=True, text=True, timeout=seconds + 120)
             line = res.stdout.strip().splitlines()[-1] if res.stdout.strip() else "{}"
-            out[mode] = json.loads(line)
+            return json.loads(line)
         except Exception as exc:  # noqa: BLE001
-            out[mode] = {"error": repr(exc)}
-    out["workload"] = ("Poisson 20k req/s, 50/50 detect/precode, B in {64,128,256}, "
-                       "U in {8,16,32}, 16/64/256-QAM, 12-1200 subcarriers, 1-14 symbols, "
-                       "SNR 5-25 dB, K=min(U/4,8); latency from scheduled arrival")
+            return {"error": repr(exc)}
+
+    out = {mode: one(mode, 20000) for mode in ("served", "plain")}
+    out["low_load"] = {}
+    for rate in (500, 5000):
+        for mode in ("served", "plain"):
+            r = one(mode, rate)
+            out["low_load"][f"{mode}_{rate}"] = {k: r.get(k) for k in
+                                                 ("lat_p50_ms", "lat_p99_ms",
+                                                  "device_service_p50_p99_ms", "completed",
+                                                  "error") if k in r}
+    out["workload"] = ("Poisson 20k req/s (and 500, 5000 req/s), 50/50 detect/precode, "
+                       "B in {64,128,256}, U in {8,16,32}, 16/64/256-QAM, 12-1200 subcarriers, "
+                       "1-14 symbols, SNR 5-25 dB, K=min(U/4,8); latency from scheduled "
+                       "arrival")
     return out
 
 
@@ -656,7 +686,7 @@ def run_ours(args):
     # end-to-end through the host-memory ABI (pinned buffers, copies timed)
     e2e = None
     if not args.no_e2e:
-        ne = min(n, 8 * NSC)
+        ne = n
         Hh = H[:ne].cpu().pin_memory()
         Yh = Y[:ne].cpu().pin_memory()
         Th = T[:ne].cpu().pin_memory()
@@ -752,11 +782,25 @@ def run_ours(args):
                          f"workers for {args.cpu_seconds:.0f} s each"}
 
     if rank == 0:
+        step_gbs = (det_bytes + pre_bytes) * world / (ms_step / 1e3) / 1e9
+        detail = {
+            "detect_solves_per_s": round(n * R * world / (det_ms / 1e3), 1),
+            "precode_solves_per_s": round(n * R * world / (pre_ms / 1e3), 1),
+            "llrs_per_s": round(llrs, 1),
+            "latency_ms": {"slot_p50": round(lat[len(lat) // 2], 4),
+                           "slot_p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4),
+                           "slot_what": "one 1200x14 slot, detect + precode, one launch each"},
+            "batched": batched, "large_256x32": large, "neumann": neumann, "cgls": cgls,
+            "sweep_128": sweep, "serving": serving, "plain_fp32": plain,
+        }
+        srv = serving or {}
+        low = srv.get("low_load", {})
         line = {
             "metric": "CG solves/s (detect + precode) at B=128, U=16, 64-QAM, R=14, K=3",
             "value": round(value, 1), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[args.precision],
             "data": "synthetic (seeded i.i.d. CN(0,1) channels, Gray 64-QAM, AWGN at 10 dB)",
             "config": {"workload": f"uplink CG-D + downlink CG-P, B={B}, U={Un}, 64-QAM, "
                                    f"{NSC} subcarriers x {R} symbols per slot, K={K}, "
@@ -766,32 +810,33 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (%.2f GB read per step)" %
                              ((det_bytes + pre_bytes) / 1e9),
                        "parallelism": f"replicas x{world}"},
-            "llrs_per_s": round(llrs, 1),
-            "detect_solves_per_s": round(n * R * world / (det_ms / 1e3), 1),
-            "precode_solves_per_s": round(n * R * world / (pre_ms / 1e3), 1),
             "detect_ms": round(det_ms, 4), "precode_ms": round(pre_ms, 4),
-            "precode_gbs": round(pre_gbs, 1),
-            "latency_ms": {"slot_p50": round(lat[len(lat) // 2], 4),
-                           "slot_p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4),
-                           "slot_what": "one 1200x14 slot, detect + precode, one launch each",
-                           "served_p50": (serving or {}).get("served", {}).get("lat_p50_ms"),
-                           "served_p99": (serving or {}).get("served", {}).get("lat_p99_ms"),
-                           "plain_p50": (serving or {}).get("plain", {}).get("lat_p50_ms"),
-                           "plain_p99": (serving or {}).get("plain", {}).get("lat_p99_ms")},
-            "batched": batched,
-            "large_256x32": large,
-            "neumann": neumann,
-            "cgls": cgls,
-            "sweep_128": sweep,
-            "serving": serving,
+            "step_frac": round(step_gbs / peaks["hbm_gbs"], 4),
+            "precode_frac": round(pre_gbs / peaks["hbm_gbs"], 4),
             "roofline": roofline,
-            "plain_fp32": plain,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
             "clocks": ck,
+            "latency_ms": {"slot_p50": detail["latency_ms"]["slot_p50"],
+                           "served_p50": srv.get("served", {}).get("lat_p50_ms"),
+                           "served_p99": srv.get("served", {}).get("lat_p99_ms"),
+                           "plain_p50": srv.get("plain", {}).get("lat_p50_ms"),
+                           "served_500_p50": low.get("served_500", {}).get("lat_p50_ms"),
+                           "plain_500_p50": low.get("plain_500", {}).get("lat_p50_ms")},
         }
+        if batched and "error" not in batched:
+            line["batched"] = {k: batched.get(k) for k in ("ms_per_run", "gb_per_s", "frac_hbm",
+                                                           "precision", "schedule")}
+            line["batched"]["plain_ms"] = batched["plain_one_launch_per_problem"]["ms"]
+        if large:
+            line["large_256x32"] = {k: large.get(k) for k in (
+                "detect_ms", "precode_ms", "detect_frac_hbm", "precode_frac_hbm",
+                "exact_tracker_detect_ms", "exact_tracker_fp32_detect_ms")}
+        print("detail: " + json.dumps(detail), file=sys.stderr)
+        sys.stderr.flush()
         print(json.dumps(line))
+        sys.stdout.flush()
     if dist:
         dist.destroy_process_group()
     _ = np, math

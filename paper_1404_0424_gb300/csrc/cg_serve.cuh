@@ -461,8 +461,12 @@ __device__ __forceinline__ void serve_poll_host(const ServeArgs& s) {
   atomicMax(&s.class_head[kServeTotal], total);
 }
 
-// Idle warps that read host memory in each 2 us window: 1 in kPollSlots.
-constexpr int kPollSlots = 256;
+// Idle warps that read host memory in each window of 2^kPollWindowShift ns:
+// 1 in kPollSlots. An idle warp sleeps at most kIdleSleepNs between looks,
+// so a request published at low load waits about one window to be seen.
+constexpr int kPollSlots = 128;
+constexpr int kPollWindowShift = 9;
+constexpr unsigned kIdleSleepNs = 512;
 
 // Each warp serves its home class (warps are spread evenly over the classes)
 // while that class has work, and otherwise the next class in turn that has
@@ -497,12 +501,13 @@ __global__ void __launch_bounds__(kServeThreads, 1)
         }
         if (pick == -1) {
           const unsigned long long now = global_timer_ns();
-          if (int((now >> 11) % kPollSlots) == gw % kPollSlots) serve_poll_host(s);
+          if (int((now >> kPollWindowShift) % kPollSlots) == gw % kPollSlots)
+            serve_poll_host(s);
           if (now - t_idle > s.idle_ns) {
             pick = -2;
           } else {
             __nanosleep(sleep_ns);
-            sleep_ns = sleep_ns < 2048 ? 2 * sleep_ns : 2048;
+            sleep_ns = sleep_ns < kIdleSleepNs ? 2 * sleep_ns : kIdleSleepNs;
           }
         }
       }
