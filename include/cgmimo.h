@@ -71,7 +71,7 @@ extern "C" {
 #define CG_SINR_APPROX 0  /* Eqs. 11-13: diagonal recursion, rho = G_ii / N0 */
 #define CG_SINR_EXACT 1   /* Eq. 10 and the B = L_K G, C = B L_K^H expressions */
 
-/* How e = A p is formed inside Algorithm 1 (line 9).
+/* How e = A p is formed inside the CG iterations of Algorithm 1.
  * CG_AMUL_IMPLICIT forms no Gram: each product costs 2 B U complex
  * multiply-adds per right-hand side, done in FP32 on the CUDA cores whatever
  * the precision field says (there is no Gram, and the matched filter is an
@@ -127,7 +127,7 @@ typedef struct cg_params {
   int32_t precision;
 } cg_params;
 
-/* CG-D soft-output detection (Sec. III-B, Algorithm 1 with lines 15-16):
+/* CG-D soft-output detection (Sec. III-B, Algorithm 1 with the SINR tracker):
  * b = H^H y, A = H^H H + (N0/Es) I, K CG iterations, the chosen SINR tracker,
  * then x_hat, mu, rho and max-log LLRs (Eq. 4). H and Y must be 8-byte
  * aligned; any of xhat, mu, rho, llr, status may be NULL (not written).
@@ -137,7 +137,7 @@ int cg_detect(const cg_params* p, int64_t n_inst, const void* H, const void* Y,
               void* stream);
 
 /* CG-P precoding (Sec. III-D): b = t, A = H_d H_d^H + (N0/Es) I with
- * H_d = H_u^H, K CG iterations, q = H_d^H v_K (Algorithm 1 line 20).
+ * H_d = H_u^H, K CG iterations, q = H_d^H v_K (Sec. III-D).
  * With normalize != 0 the power-normalised s = q / ||q||_2 (Sec. II-B) is
  * written to q instead. qnorm and status may be NULL. The sinr_mode and
  * qam_bits fields are ignored. */

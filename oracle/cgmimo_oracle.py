@@ -27,7 +27,7 @@ CUDA path implements independently):
     g; the level index is j with gray(j) = j ^ (j >> 1) = g and the level is
     (2j - (L-1)) * c * sqrt(Es), L = 2^(q/2), c = sqrt(3 / (2 (M - 1))).
   * LLR sign as printed in Eq. 4: L > 0 favours bit 1.
-  * alpha uses Re(p^H e) (real in exact arithmetic, Algorithm 1 line 10).
+  * alpha uses Re(p^H e) (real in exact arithmetic, the step size of Algorithm 1).
   * The L-recursions of Eq. 10 and Eq. 11 start from L_1 = alpha_1 I and are
     applied for k >= 2, with alpha_k = 1, beta_k = 0 and L_k = 0 for k < 1.
   * Breakdown: if ||r_{k-1}||^2 is not > 0 or Re(p^H e) is not > 0, CG stops
@@ -47,7 +47,7 @@ STATUS_MU_NONPOS = 2
 
 
 # ----------------------------------------------------------------------------
-# Regularised Gram, matched filter (Sec. III-B, Eq. 7; Algorithm 1 line 5)
+# Regularised Gram, matched filter (Sec. III-B, Eqs. 7, 8; Algorithm 1)
 # ----------------------------------------------------------------------------
 
 def gram(H: np.ndarray) -> np.ndarray:
@@ -57,13 +57,13 @@ def gram(H: np.ndarray) -> np.ndarray:
 
 
 def regularised_gram(H: np.ndarray, N0: float, Es: float) -> np.ndarray:
-    """A = H^H H + rho_u^-1 I with rho_u = Es/N0 (Eq. 7; Algorithm 1 line 5)."""
+    """A = H^H H + rho_u^-1 I with rho_u = Es/N0 (Eq. 7; Algorithm 1)."""
     U = H.shape[1]
     return gram(H) + (N0 / Es) * np.eye(U)
 
 
 def matched_filter(H: np.ndarray, y: np.ndarray) -> np.ndarray:
-    """b = H^H y (Algorithm 1 line 5)."""
+    """b = H^H y (Eq. 8; Algorithm 1)."""
     H = np.asarray(H, dtype=np.complex128)
     return H.conj().T @ np.asarray(y, dtype=np.complex128)
 
@@ -157,7 +157,7 @@ def mmse_exact(H: np.ndarray, y: np.ndarray, N0: float, Es: float) -> dict:
 # ----------------------------------------------------------------------------
 
 def conjugate_gradient(A: np.ndarray, b: np.ndarray, K: int) -> dict:
-    """K iterations of Algorithm 1 (lines 7-14) on A g = b.
+    """K CG iterations of Algorithm 1 on A g = b.
 
     Returns v_K, the per-iteration alpha_k and beta_k (k = 1..K_done), every
     iterate v_0..v_{K_done}, and a breakdown flag (module docstring).
@@ -174,17 +174,17 @@ def conjugate_gradient(A: np.ndarray, b: np.ndarray, K: int) -> dict:
         if not rr > 0:
             broke = True
             break
-        e = A @ p                               # line 9
+        e = A @ p
         pe = np.real(np.vdot(p, e))             # p^H e
         if not pe > 0:
             broke = True
             break
-        alpha = rr / pe                         # line 10
-        v = v + alpha * p                       # line 11
-        r = r - alpha * e                       # line 12
+        alpha = rr / pe
+        v = v + alpha * p
+        r = r - alpha * e
         rr_new = np.real(np.vdot(r, r))
-        beta = rr_new / rr                      # line 13
-        p = r + beta * p                        # line 14
+        beta = rr_new / rr
+        p = r + beta * p
         rr = rr_new
         alphas.append(alpha)
         betas.append(beta)
@@ -421,8 +421,8 @@ def cg_detect(H: np.ndarray, Y: np.ndarray, N0: float, Es: float, K: int,
 def cg_precode_one(H: np.ndarray, t: np.ndarray, N0: float, Es: float, K: int) -> dict:
     """Algorithm 1 for precoding one transmit vector t (Sec. III-D).
 
-    H_d = H_u^H, A = H_d H_d^H + rho_d^-1 I (Algorithm 1 line 6), b = t,
-    K CG iterations, then q_K = H_d^H v_K (line 20) and s = q / ||q||_2
+    H_d = H_u^H, A = H_d H_d^H + rho_d^-1 I (Sec. III-D), b = t,
+    K CG iterations, then q_K = H_d^H v_K (Sec. III-D) and s = q / ||q||_2
     (power normalisation, Sec. II-B).
     """
     Hd = np.asarray(H, dtype=np.complex128).conj().T

@@ -6,6 +6,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "cgmimo.h"
 #include "host_checks.h"
 #include "launch.cuh"
@@ -59,6 +61,47 @@ int check_supported(const cg_params* p) {
   return CG_OK;
 }
 
+// cuTensorMapEncodeTiled, taken from the driver through the runtime once
+// (null if the driver does not offer it: the calls then use cp.async).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// 3-D tiled map of n matrices of rows x cols complex values stored as FP32
+// pairs: dims {2 cols, rows, n}, box {bx, by, 1} elements, zero fill.
+bool encode_map(CUtensorMap* m, const void* base, int64_t n, int rows, int cols, int bx, int by,
+                CUtensorMapSwizzle sw) {
+  auto enc = tensor_map_encoder();
+  if (enc == nullptr || n > INT32_MAX) return false;
+  const cuuint64_t dims[3] = {cuuint64_t(2 * cols), cuuint64_t(rows), cuuint64_t(n)};
+  const cuuint64_t strides[2] = {cuuint64_t(8) * cols, cuuint64_t(8) * cols * rows};
+  const cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps of the warp kernels' staging (DetectArgs::tmH, tmY): H boxes
+// of 8 antennas x min(UT, 16) users, Y boxes of 16 rows x 8 antennas. Only
+// for the layout the vector path reads (U == UT, B even, 16-byte aligned).
+bool detect_maps(DetectArgs* a, int UT) {
+  if (a->U != UT || a->B % 2 || !aligned(a->H, 16) || !aligned(a->Y, 16)) return false;
+  const int ub = UT < 16 ? UT : 16;
+  return encode_map(&a->tmH, a->H, a->n_inst, a->B, a->U, 2 * ub, 8,
+                    UT == 8 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B) &&
+         encode_map(&a->tmY, a->Y, a->n_inst, a->R, a->B, 16, 16, CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
 // Tensor-core operand type (0 = BF16, 1 = FP16) and hi+lo split of a precision mode.
 void tc_mode(int precision, int* el, bool* x3) {
   *el = (precision == CG_PREC_BF16 || precision == CG_PREC_BF16X3) ? 0 : 1;
@@ -99,6 +142,7 @@ int detect_device(const cg_params* p, int64_t n_inst, const void* H, const void*
     bool x3;
     tc_mode(p->precision, &el, &x3);
     const int UT = padded_users(p->U);
+    if (!a.exact) a.tma = detect_maps(&a, UT) ? 1 : 0;
     err = a.exact ? launch_detect_warp_exact(UT, el, x3, a, s)
                   : launch_detect_warp(UT, el, x3, a, s);
   }

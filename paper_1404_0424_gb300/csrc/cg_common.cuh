@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (the type only; nothing links the driver library)
 #include <cuda_runtime.h>
 
 namespace cgm {
@@ -60,6 +61,44 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
       : "memory");
 }
 
+// 3-D tiled tensor copy (TMA) global -> shared of the box at element
+// coordinates (x, y, z) of `map`, completion counted on `bar` in bytes. The
+// map must sit in kernel-parameter (__grid_constant__), constant or global
+// memory; dst is aligned to the map's swizzle span; x * element size is a
+// multiple of 16 bytes. Out-of-range elements of the box arrive as zeros.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// As tma_load_3d, with dst and bar given as shared-space addresses.
+__device__ __forceinline__ void tma_load_3d_s(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                              int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_s(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx_s(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// Fetches a tensor map into the TMA unit's descriptor cache ahead of use.
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -84,6 +123,30 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_try_wait_s(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_test_wait_s(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for phase `parity` of `bar` to complete; gives up after timeout_ns
 // of global time and returns false. try_wait may suspend the thread for a
 // while by itself, so limits under 1 us poll with the non-blocking
@@ -94,6 +157,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   const uint64_t t0 = global_timer_ns();
   while (true) {
     if (poll ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
+    if (global_timer_ns() - t0 > timeout_ns) return false;
+    if (!poll) __nanosleep(64);
+  }
+}
+
+// mbar_wait_bounded on a shared-space address. The first try_wait is made
+// before the clock is read, so a phase that is already complete costs one
+// instruction.
+__device__ __forceinline__ bool mbar_wait_bounded_s(uint32_t bar, uint32_t parity,
+                                                    uint64_t timeout_ns) {
+  const bool poll = timeout_ns < 1000;
+  if (poll ? mbar_test_wait_s(bar, parity) : mbar_try_wait_s(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (true) {
+    if (poll ? mbar_test_wait_s(bar, parity) : mbar_try_wait_s(bar, parity)) return true;
     if (global_timer_ns() - t0 > timeout_ns) return false;
     if (!poll) __nanosleep(64);
   }

@@ -1,5 +1,5 @@
 // FP32 kernels with the implicit product e = H^H (H p) + sigma p in
-// Algorithm 1 (line 9): no Gram matrix is formed. One CTA owns an instance;
+// Algorithm 1 with e = A p formed as H^H (H p) + sigma p: no Gram matrix is formed. One CTA owns an instance;
 // H stays in shared memory for the whole solve, and one group of UT lanes
 // runs the CG of one right-hand side (lane i owns user i):
 //   w = H p   lane i forms w_b for antennas b = i, i + UT, ... (rows of H,
@@ -80,7 +80,7 @@ __device__ __forceinline__ float2 implicit_hhw(const float2* __restrict__ sH, in
   return e;
 }
 
-// Algorithm 1 lines 7-14 for right-hand sides r = g, g + NG, ... with the
+// The CG iterations of Algorithm 1 for right-hand sides r = g, g + NG, ... with the
 // implicit product; b in sB[r], v_K into sX[r]. With `track` the
 // approximate tracker of Eqs. 11-13 as in cg_groups (D_ii = G_ii + sigma).
 template <int UT, int NTHR>
@@ -113,7 +113,7 @@ __device__ __forceinline__ void implicit_cg_groups(const float2* __restrict__ sH
         broke = true;
         break;
       }
-      // e = H^H (H p) + sigma p (line 9, implicit)
+      // e = H^H (H p) + sigma p (implicit)
       sP[i] = p;
       __syncwarp(mask);
       implicit_hp<UT>(sH, B, U, sP, sW);
@@ -125,14 +125,14 @@ __device__ __forceinline__ void implicit_cg_groups(const float2* __restrict__ sH
         broke = true;
         break;
       }
-      const float alpha = rr / pe;  // line 10
-      v.x = fmaf(alpha, p.x, v.x);  // line 11
+      const float alpha = rr / pe;
+      v.x = fmaf(alpha, p.x, v.x);  // v += alpha p
       v.y = fmaf(alpha, p.y, v.y);
-      res.x = fmaf(-alpha, e.x, res.x);  // line 12
+      res.x = fmaf(-alpha, e.x, res.x);  // r -= alpha e
       res.y = fmaf(-alpha, e.y, res.y);
       const float rrn = group_sum_compensated<UT>(res.x * res.x + res.y * res.y, mask);
-      const float beta = rrn / rr;  // line 13
-      p.x = fmaf(beta, p.x, res.x);  // line 14
+      const float beta = rrn / rr;
+      p.x = fmaf(beta, p.x, res.x);  // p = r + beta p
       p.y = fmaf(beta, p.y, res.y);
       rr = rrn;
       const float lk = (k == 1) ? alpha
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) detect_implicit_kernel(cons
   for (int64_t n = blockIdx.x; n < a.n_inst; n += gridDim.x) {
     if (!implicit_stage_detect<NTHR>(a, P.io, smem, bar, &parity, n)) return;
     if (tid == 0) *sStatus = 0;
-    // matched filters b = H^H y (Algorithm 1 line 5) and G_ii = ||h_i||^2
+    // matched filters b = H^H y (Eq. 8) and G_ii = ||h_i||^2
     for (int e = tid; e < R * UT; e += NTHR) {
       const int r = e / UT, i = e - r * UT;
       float2 s = make_float2(0.f, 0.f);
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) precode_implicit_kernel(con
       __syncthreads();
     }
     if (tid == 0) *sStatus = 0;
-    // b = t (Algorithm 1 line 6), padded to UT users
+    // b = t (Sec. III-D), padded to UT users
     for (int e = tid; e < R * UT; e += NTHR) {
       const int r = e / UT, i = e - r * UT;
       sBm[e] = (i < U) ? sT[r * U + i] : make_float2(0.f, 0.f);
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) precode_implicit_kernel(con
       implicit_cg_groups<UT, NTHR>(sH, B, U, a.sigma, sBm, nullptr, R, a.K, 0.f, false, sP, sW,
                                    sX, nullptr, nullptr, sKd, sStatus);
     }
-    // line 20: q = H v by the group that owns v, ||q||^2 = sum_b |q_b|^2
+    // q = H v (Sec. III-D) by the group that owns v, ||q||^2 = sum_b |q_b|^2
     if constexpr (!CGLS) {
       const int g = tid / UT, i = tid % UT;
       const unsigned mask = group_mask<UT>();

@@ -6,8 +6,8 @@
 //   1. bulk-copy H [B][U] and the R rows of Y (or T) into shared memory,
 //   2. form G = H^H H and the matched filters b_r = H^H y_r as one register-
 //      tiled product H^H [H | Y^T] with the antenna axis split into slices
-//      (Algorithm 1 line 5), reduce the slices in a fixed order,
-//   3. run Algorithm 1 lines 7-14 with one group of UT lanes per right-hand
+//      (Algorithm 1; Eqs. 7, 8), reduce the slices in a fixed order,
+//   3. run the CG iterations of Algorithm 1 with one group of UT lanes per right-hand
 //      side (lane i owns user i; inner products are compensated group sums)
 //      and the approximate tracker of Eqs. 11-13 in the loop,
 //   4. optionally the exact tracker of Eq. 10 (CTA-cooperative, per RHS),
@@ -43,6 +43,13 @@ struct DetectArgs {
   int exact;  // CG_SINR_EXACT
   int bulk;   // inputs may be fetched with 1-D bulk copies
   uint64_t wait_ns;  // limit of the wait for an instance's bulk copies (cg_set_wait_limit)
+  // Tensor maps of H ([n][B][U] complex as FP32, box 8 antennas x 16 users,
+  // 128-byte swizzle; 8 users: 64-byte swizzle) and Y ([n][R][B], box 16 rows
+  // x 8 antennas), valid when tma != 0. The warp kernels stage their Gram
+  // k-steps through them; a kernel that reads them takes its arguments as
+  // __grid_constant__.
+  int tma;
+  CUtensorMap tmH, tmY;
 };
 
 struct PrecodeArgs {
@@ -58,6 +65,8 @@ struct PrecodeArgs {
   int bulk_h;  // H may be fetched with bulk copies
   int bulk_t;  // T may be fetched with bulk copies
   uint64_t wait_ns;  // limit of the wait for an instance's bulk copies (cg_set_wait_limit)
+  int tma;         // tmH is valid (as in DetectArgs)
+  CUtensorMap tmH;
 };
 
 // Byte offsets into dynamic shared memory; computed identically on host and
@@ -303,7 +312,7 @@ __device__ __forceinline__ void cg_groups(const float2* __restrict__ sA,
         broke = true;
         break;
       }
-      // e = A p (line 9); A[j][i] = conj(A[i][j]) keeps the reads contiguous
+      // e = A p; A[j][i] = conj(A[i][j]) keeps the reads contiguous
       float2 e = make_float2(0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < UT; ++j) {
@@ -318,14 +327,14 @@ __device__ __forceinline__ void cg_groups(const float2* __restrict__ sA,
         broke = true;
         break;
       }
-      const float alpha = rr / pe;  // line 10
-      v.x = fmaf(alpha, p.x, v.x);  // line 11
+      const float alpha = rr / pe;
+      v.x = fmaf(alpha, p.x, v.x);  // v += alpha p
       v.y = fmaf(alpha, p.y, v.y);
-      res.x = fmaf(-alpha, e.x, res.x);  // line 12
+      res.x = fmaf(-alpha, e.x, res.x);  // r -= alpha e
       res.y = fmaf(-alpha, e.y, res.y);
       const float rrn = group_sum_compensated<UT>(res.x * res.x + res.y * res.y, mask);
-      const float beta = rrn / rr;  // line 13
-      p.x = fmaf(beta, p.x, res.x);  // line 14
+      const float beta = rrn / rr;
+      p.x = fmaf(beta, p.x, res.x);  // p = r + beta p
       p.y = fmaf(beta, p.y, res.y);
       rr = rrn;
       // Eq. 11 on the diagonal: l_1 = alpha_1, then the three-term recursion
@@ -622,7 +631,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) detect_kernel(const DetectA
     }
     if (tid == 0) *sStatus = 0;
 
-    // ---- step 2: G and the matched filters (Algorithm 1 line 5)
+    // ---- step 2: G and the matched filters (Algorithm 1; Eqs. 7, 8)
     float2 acc[TM][TN];
     int tile, slice;
     gram_tile<UT, true>(sH, sY, P.YS, a.B, U, R, P, acc, tile, slice);
@@ -662,7 +671,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) detect_kernel(const DetectA
       issue_detect_copies(a, P, smem, bar, next);
     }
 
-    // ---- step 3: Algorithm 1 lines 7-16
+    // ---- step 3: the CG iterations and tracker updates of Algorithm 1
     cg_groups<UT, NTHR>(sA, sBm, sGd, R, a.K, a.N0, true, sX, sMu, sRho, sAB, sKd, sStatus);
     __syncthreads();
 
@@ -756,13 +765,13 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) precode_kernel(const Precod
       __syncthreads();
     }
     if (tid == 0) *sStatus = 0;
-    // Right-hand sides b = t (Algorithm 1 line 6), padded to UT users
+    // Right-hand sides b = t (Sec. III-D), padded to UT users
     for (int e = tid; e < R * UT; e += NTHR) {
       const int r = e / UT, i = e - (e / UT) * UT;
       sV[e] = (i < U) ? sT[r * U + i] : make_float2(0.f, 0.f);
     }
 
-    // ---- step 2: A = H_d H_d^H + sigma I = H^H H + sigma I (Algorithm 1 line 6)
+    // ---- step 2: A = H_d H_d^H + sigma I = H^H H + sigma I (Sec. III-D)
     float2 acc[TM][TN];
     int tile, slice;
     gram_tile<UT, false>(sH, nullptr, 0, B, U, 1, P, acc, tile, slice);
@@ -824,7 +833,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) precode_kernel(const Precod
     }
     __syncthreads();
 
-    // ---- step 3: Algorithm 1 lines 7-14 (sV <- v_K), then ||q||^2 = v^H G v
+    // ---- step 3: the CG iterations of Algorithm 1 (sV <- v_K), then ||q||^2 = v^H G v
     cg_groups<UT, NTHR>(sA, sV, nullptr, R, a.K, 1.f, false, sV, nullptr, nullptr, nullptr,
                         sKd, sStatus);
     {
@@ -842,7 +851,7 @@ __global__ void __launch_bounds__(TileCfg<UT>::NTHR) precode_kernel(const Precod
     }
     __syncthreads();
 
-    // ---- step 4: q = H_d^H v = H v (line 20), optionally s = q / ||q|| (Sec. II-B).
+    // ---- step 4: q = H_d^H v = H v (Sec. III-D), optionally s = q / ||q|| (Sec. II-B).
     // Work item = (antenna b, group of RC right-hand sides); the user index is
     // rotated by the lane so that a warp's H reads fall in distinct banks.
     {

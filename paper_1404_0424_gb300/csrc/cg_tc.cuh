@@ -3,9 +3,10 @@
 //
 // Every dense contraction of the method runs on the tensor cores as
 // mma.sync.m16n8k16 with FP16 or BF16 operands and FP32 accumulation:
-//   * G = H^H H and the matched filters H^H Y (Algorithm 1 line 5),
-//   * e = A p for all right-hand sides of an instance at once (line 9),
-//   * q = H v for all right-hand sides (line 20, precoding).
+//   * G = H^H H and the matched filters H^H Y (Algorithm 1; Eqs. 7, 8),
+//   * e = A p for all right-hand sides of an instance at once (the CG
+//     iterations of Algorithm 1),
+//   * q = H v for all right-hand sides (precoding, Sec. III-D).
 // A complex product is split into real and imaginary accumulators with the
 // contraction index k = (antenna or user, re/im): an m16n8k16 A-fragment
 // register then holds exactly one complex64 element packed as (re, im), so

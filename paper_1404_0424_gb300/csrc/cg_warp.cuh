@@ -2,21 +2,25 @@
 //
 // One warp owns one instance (a channel H with its R <= 16 right-hand sides)
 // from its first load to its last store, so no CTA barrier is involved:
-//   1. CG-D stages H and Y through a per-warp shared-memory ring of 16-byte
-//      cp.async copies, RING_STAGES k-steps of 8 antennas ahead of the
-//      products (the first stages of the next instance are issued before the
-//      CG of the current one); CG-P, which reads H a second time for
+//   1. CG-D stages H and Y through a per-warp shared-memory ring, STAGES - 1
+//      k-steps of 8 antennas ahead of the products (the first stages of the
+//      next instance are issued before the CG of the current one), filled
+//      by one lane's tensor copies (TMA) in single calls and by the lanes'
+//      cp.async copies otherwise; CG-P, which reads H a second time for
 //      q = H v, loads it with 16-byte register loads through L1;
 //   2. G = H^H H and the transposed matched filters B^T = Y^T conj(H)
-//      (Algorithm 1 line 5) accumulate on the tensor cores;
-//   3. Algorithm 1 lines 7-16 run entirely in registers. Users are numbered
+//      (the Gram and matched-filter step of Algorithm 1) accumulate on the
+//      tensor cores;
+//   3. the CG iterations and tracker updates of Algorithm 1 run entirely in
+//      registers. Users are numbered
 //      in a "position" order chosen so that the Gram accumulators of a lane
 //      are exactly its B fragments of e = A p, and the matched-filter
 //      accumulators are exactly the layout of the CG vectors: accumulator
 //      row = right-hand side, accumulator column = position. Inner products
 //      over users are quad shuffles (compensated sums);
 //   4. x_hat, mu, rho and the max-log LLRs of Eq. 4 (CG-D) or q = H v (CG-P,
-//      Algorithm 1 line 20) are stored from the registers that hold them.
+//      the precoding output of Algorithm 1) are stored from the registers that
+//      hold them.
 //
 // Position P (0 <= P < 8 NB) holds user pos_user(P). With 16 or 32 users the
 // 8-blocks interleave in pairs (P = 16 m + 8 h + w holds user 16 m + 2 w + h),
@@ -33,8 +37,15 @@
 
 namespace cgm {
 
-// Load stages in flight per warp (16-byte cp.async copies into a ring).
-constexpr int RING_STAGES = 4;
+// Load stages of the per-warp ring (16-byte cp.async copies), by padded
+// user count; 32 users have no shared memory for more than 4.
+#ifndef CGM_RING8
+#define CGM_RING8 4
+#endif
+
+#ifndef CGM_RING16
+#define CGM_RING16 4
+#endif
 
 template <int UT>
 struct WarpCfg {
@@ -42,6 +53,7 @@ struct WarpCfg {
   static constexpr int NB = UT / 8;              // 8-position blocks
   static constexpr int MT = UT == 32 ? 2 : 1;    // 16-position m-tiles of the Gram rows
   static constexpr int PLANES = 2 * MT + 2;      // ring planes per stage: H rows, then Y
+  static constexpr int STAGES = UT == 32 ? 4 : UT == 16 ? CGM_RING16 : CGM_RING8;
   // The CG B fragments of A are kept hi|lo, and times i as well unless that
   // would not fit (32 users form i A on the fly).
   static constexpr bool STORE_IM = UT <= 16;
@@ -51,14 +63,16 @@ struct WarpCfg {
   // resident CTAs per SM targeted: 8 users fit 4 CTAs in 128 registers; 16
   // users run faster at 3 CTAs without spills than at 4 with them
   static constexpr int MINB = UT == 32 ? 2 : UT == 16 ? CGM_WARP_MINB : 4;
-  // per warp: a ring of RING_STAGES load stages (PLANES planes of 16 bytes
+  // per warp: a ring of STAGES load stages (PLANES planes of 16 bytes
   // per lane each), the CG B fragments (one uint2 per lane and fragment), and
   // alpha_k, beta_k of the 16 right-hand-side rows for the tracker (K <= UT)
-  static constexpr uint32_t RING_BYTES = uint32_t(RING_STAGES) * PLANES * 32u * 16u;
+  static constexpr uint32_t RING_BYTES = uint32_t(STAGES) * PLANES * 32u * 16u;
   static constexpr uint32_t FRAG_BYTES = uint32_t(NFRAG) * 32u * 8u;
   static constexpr uint32_t AB_BYTES = uint32_t(UT) * 16u * 8u;
   static constexpr uint32_t WARP_BYTES = RING_BYTES + FRAG_BYTES + AB_BYTES;
   static constexpr uint32_t SMEM = uint32_t(WARPS) * WARP_BYTES;       // CG-D
+  // CG-D staged by TMA: the warps' slices, then STAGES mbarriers per warp
+  static constexpr uint32_t TMA_SMEM = SMEM + uint32_t(WARPS) * STAGES * 8u;
   static constexpr uint32_t PRE_SMEM = uint32_t(WARPS) * FRAG_BYTES;  // CG-P: fragments only
 };
 
@@ -114,7 +128,7 @@ __device__ __forceinline__ void ring_gram_issue(unsigned char* ring, const float
   constexpr int PL = WarpCfg<UT>::PLANES, MT = WarpCfg<UT>::MT;
   if (ks < KS) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int slot = ks % RING_STAGES;
+    const int slot = ks % WarpCfg<UT>::STAGES;
     const int b0 = 8 * ks + 2 * t, b1 = b0 + 1;
     const bool ok = b0 < B;
     if constexpr (UT == 8) {
@@ -140,7 +154,7 @@ template <int UT, bool MF>
 __device__ __forceinline__ void ring_gram_read(unsigned char* ring, int ks,
                                                float2 (&h)[WarpCfg<UT>::MT][4], float2 (&y)[4]) {
   constexpr int PL = WarpCfg<UT>::PLANES, MT = WarpCfg<UT>::MT;
-  const int slot = ks % RING_STAGES;
+  const int slot = ks % WarpCfg<UT>::STAGES;
   if constexpr (UT == 8) {
     h[0][0] = *reinterpret_cast<const float2*>(ring_at<PL>(ring, slot, 0));
     h[0][2] = *reinterpret_cast<const float2*>(ring_at<PL>(ring, slot, 1));
@@ -166,13 +180,134 @@ __device__ __forceinline__ void ring_gram_read(unsigned char* ring, int ks,
   }
 }
 
-// First RING_STAGES - 1 k-steps of an instance's Gram.
+// First STAGES - 1 k-steps of an instance's Gram.
 template <int UT, bool MF>
 __device__ __forceinline__ void ring_gram_prologue(unsigned char* ring, const float2* H,
                                                    const float2* Y, int B, int R) {
   const int KS = (B + 7) / 8;
 #pragma unroll
-  for (int ks = 0; ks < RING_STAGES - 1; ++ks) ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, ks);
+  for (int ks = 0; ks < WarpCfg<UT>::STAGES - 1; ++ks) ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, ks);
+}
+
+// ---------------------------------------------------------------------------
+// Gram k-steps staged by the tensor memory accelerator (TMA)
+// ---------------------------------------------------------------------------
+
+// The same ring, filled by one lane with two 3-D tensor copies per k-step
+// (DetectArgs::tmH, tmY) that complete on the slot's mbarrier. A slot holds
+// the H box of each m-tile (8 antenna rows of 16 users, 128 bytes a row,
+// 128-byte swizzle: 16-byte chunk c of row r sits at chunk c ^ r; with 8
+// users, rows of 64 bytes with 64-byte swizzle: chunk c of row r at
+// c ^ (r / 2)), then at byte 1024 MT the Y box (16 right-hand-side rows of
+// 8 antennas, 64 bytes a row, unswizzled; rows past R and antennas past B
+// arrive as zeros). Lane (g, t) reads exactly the fragments the cp.async
+// ring gives it, without bank conflicts. Slots sit at multiples of 1024
+// bytes, the span of the swizzle pattern.
+struct TmaRing {
+  uint32_t bar;  // shared-space address of this warp's STAGES mbarriers (8 bytes apart)
+  uint32_t st;   // bits 0-7: parity of each slot's next phase; 8-15: slots in flight
+};
+
+__device__ __forceinline__ void tma_ring_init(TmaRing& tr, uint32_t bar, int stages) {
+  tr.bar = bar;
+  tr.st = 0;
+  if ((threadIdx.x & 31) == 0) {
+    for (int i = 0; i < stages; ++i) mbar_init_s(bar + 8 * i, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+}
+
+// Issues k-step ks (< KS) of instance z into its slot. Every lane has read
+// the slot's previous contents into registers before the __syncwarp.
+template <int UT, bool MF>
+__device__ __forceinline__ void tma_gram_issue(unsigned char* ring, TmaRing& tr,
+                                               const CUtensorMap* tmH, const CUtensorMap* tmY,
+                                               int z, int KS, int ks) {
+  if (ks >= KS) return;
+  constexpr int MT = WarpCfg<UT>::MT, PL = WarpCfg<UT>::PLANES;
+  constexpr uint32_t HBOX = UT == 8 ? 512u : 1024u;
+  const int slot = ks % WarpCfg<UT>::STAGES;
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    const uint32_t base = smem_addr(ring) + slot * PL * 512;
+    const uint32_t bar = tr.bar + 8 * slot;
+    mbar_arrive_expect_tx_s(bar, MT * HBOX + (MF ? 1024u : 0u));
+#pragma unroll
+    for (int m = 0; m < MT; ++m) tma_load_3d_s(base + m * 1024, tmH, 32 * m, 8 * ks, z, bar);
+    if constexpr (MF) tma_load_3d_s(base + MT * 1024, tmY, 16 * ks, 0, z, bar);
+  }
+  tr.st |= 256u << slot;
+}
+
+// First STAGES - 1 k-steps of instance z. The fence orders earlier generic
+// writes to the ring (scratch) before the tensor copies that overwrite it.
+template <int UT, bool MF>
+__device__ __forceinline__ void tma_gram_prologue(unsigned char* ring, TmaRing& tr,
+                                                  const CUtensorMap* tmH, const CUtensorMap* tmY,
+                                                  int z, int B) {
+  const int KS = (B + 7) / 8;
+  fence_proxy_async_smem();
+#pragma unroll
+  for (int ks = 0; ks < WarpCfg<UT>::STAGES - 1; ++ks)
+    tma_gram_issue<UT, MF>(ring, tr, tmH, tmY, z, KS, ks);
+}
+
+// Waits for k-step ks (bounded by wait_ns) and reads the lane's fragments;
+// false if the wait ran out (the fragments are then not valid).
+template <int UT, bool MF>
+__device__ __forceinline__ bool tma_gram_read(unsigned char* ring, TmaRing& tr, int ks,
+                                              uint64_t wait_ns,
+                                              float2 (&h)[WarpCfg<UT>::MT][4], float2 (&y)[4]) {
+  constexpr int MT = WarpCfg<UT>::MT, PL = WarpCfg<UT>::PLANES;
+  const int slot = ks % WarpCfg<UT>::STAGES;
+  const bool ok = mbar_wait_bounded_s(tr.bar + 8 * slot, (tr.st >> slot) & 1u, wait_ns);
+  tr.st ^= 1u << slot;
+  tr.st &= ~(256u << slot);
+  const unsigned char* base = ring + slot * PL * 512;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = 2 * t, r1 = 2 * t + 1;
+  if constexpr (UT == 8) {
+    h[0][0] = *reinterpret_cast<const float2*>(
+        base + r0 * 64 + ((((g >> 1) ^ (r0 >> 1)) & 3) << 4) + ((g & 1) << 3));
+    h[0][2] = *reinterpret_cast<const float2*>(
+        base + r1 * 64 + ((((g >> 1) ^ (r1 >> 1)) & 3) << 4) + ((g & 1) << 3));
+    h[0][1] = h[0][3] = make_float2(0.f, 0.f);
+  } else {
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const float4 v0 =
+          *reinterpret_cast<const float4*>(base + m * 1024 + r0 * 128 + ((g ^ r0) << 4));
+      const float4 v1 =
+          *reinterpret_cast<const float4*>(base + m * 1024 + r1 * 128 + ((g ^ r1) << 4));
+      h[m][0] = make_float2(v0.x, v0.y);
+      h[m][1] = make_float2(v0.z, v0.w);
+      h[m][2] = make_float2(v1.x, v1.y);
+      h[m][3] = make_float2(v1.z, v1.w);
+    }
+  }
+  if constexpr (MF) {
+    const float4 w0 = *reinterpret_cast<const float4*>(base + MT * 1024 + g * 64 + t * 16);
+    const float4 w1 = *reinterpret_cast<const float4*>(base + MT * 1024 + (g + 8) * 64 + t * 16);
+    y[0] = make_float2(w0.x, w0.y);
+    y[2] = make_float2(w0.z, w0.w);
+    y[1] = make_float2(w1.x, w1.y);
+    y[3] = make_float2(w1.z, w1.w);
+  }
+  return ok;
+}
+
+// Waits (bounded) for every slot still in flight, so that no copy lands in
+// shared memory after the warp is done with it.
+template <int UT>
+__device__ __forceinline__ void tma_ring_drain(TmaRing& tr) {
+#pragma unroll 1
+  for (int slot = 0; slot < WarpCfg<UT>::STAGES; ++slot)
+    if ((tr.st >> (8 + slot)) & 1u) {
+      mbar_wait_bounded_s(tr.bar + 8 * slot, (tr.st >> slot) & 1u, WAIT_TIMEOUT_NS);
+      tr.st ^= 1u << slot;
+    }
+  tr.st &= 255u;
 }
 
 // Prefetch into L1 of the 8-antenna block ks of an instance's H with UT
@@ -710,10 +845,10 @@ struct WarpCg {
     }
   }
 
-  // Lines 7-14 of Algorithm 1. res holds b on entry; rows >= R are
+  // The CG iterations of Algorithm 1. res holds b on entry; rows >= R are
   // inactive from the start. With TRACK, alpha_k and beta_k of every row are
   // kept in sAB[(k - 1) * 16 + row] for the tracker (tracker_l below).
-  // Line 7: v = 0, p = r = b (res holds b), ||r||^2 of every row.
+  // Initialisation: v = 0, p = r = b (res holds b), ||r||^2 of every row.
   __device__ __forceinline__ void init() {
     float s[2] = {0.f, 0.f};
 #pragma unroll
@@ -732,7 +867,7 @@ struct WarpCg {
     rrn[1] = s[1];
   }
 
-  // Lines 8-14 after init().
+  // The CG iterations after init().
   template <bool TRACK>
   __device__ __forceinline__ void run(const uint2* frag, float2* sAB, int R, int K) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -1147,7 +1282,7 @@ __device__ __forceinline__ void store_row_detect(const DetItem& it, int r, int t
 // ---------------------------------------------------------------------------
 
 // Loading scheme of a Gram: the warp's cp.async ring (its prologue already
-// issued, RING_STAGES - 1 k-steps ahead), 16-byte register loads one k-step
+// issued, STAGES - 1 k-steps ahead), 16-byte register loads one k-step
 // ahead (through L1), or predicated element loads for any layout.
 enum : int { LD_RING = 0, LD_VEC = 1, LD_ELEM = 2 };
 
@@ -1162,8 +1297,8 @@ __device__ __forceinline__ void gram_ring_loop(const float2* H, const float2* Y,
     apply_scale<UT, MF>(h, y, sh, sy0, sy1);
     gram_ks<UT, EL, X3, MF>(h, y, Gr, Gi, Mr, Mn);
     if (++ks >= KS) break;
-    ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, ks + RING_STAGES - 1);
-    cp_wait<RING_STAGES - 1>();
+    ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, ks + WarpCfg<UT>::STAGES - 1);
+    cp_wait<WarpCfg<UT>::STAGES - 1>();
     ring_gram_read<UT, MF>(ring, ks, h, y);
   }
 }
@@ -1200,7 +1335,8 @@ __device__ __forceinline__ void gram_direct_loop(const float2* H, const float2* 
   }
 }
 
-// Algorithm 1 line 5: G and b^T on the tensor cores, of H and Y scaled by
+// Gram and matched filters (Algorithm 1; Eqs. 7, 8): G and b^T on the
+// tensor cores, of H and Y scaled by
 // sc. Unless `given`, sc is first chosen from k-step 0 (scale_from_ks).
 template <int UT, int EL, bool X3, int LD, bool MF>
 __device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int B, int U, int R,
@@ -1221,8 +1357,8 @@ __device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int 
   constexpr bool V = LD == LD_VEC;
   float2 h[MT][4], y[4] = {};
   if constexpr (LD == LD_RING) {
-    ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, RING_STAGES - 1);
-    cp_wait<RING_STAGES - 1>();
+    ring_gram_issue<UT, MF>(ring, H, Y, B, R, KS, WarpCfg<UT>::STAGES - 1);
+    cp_wait<WarpCfg<UT>::STAGES - 1>();
     ring_gram_read<UT, MF>(ring, 0, h, y);
   } else {
     if constexpr (V)
@@ -1239,6 +1375,39 @@ __device__ __forceinline__ void warp_gram(const float2* H, const float2* Y, int 
     gram_direct_loop<UT, EL, X3, V, MF>(H, Y, B, U, R, KS, h, y, sh, sy0, sy1, Gr, Gi, Mr, Mn);
 }
 
+// warp_gram (with the matched filters) through the TMA ring, whose first
+// STAGES - 1 k-steps of instance z are in flight; false if a wait ran out.
+template <int UT, int EL, bool X3>
+__device__ __forceinline__ bool warp_gram_tma(int B, unsigned char* ring, TmaRing& tr,
+                                              const CUtensorMap* tmH, const CUtensorMap* tmY,
+                                              int z, uint64_t wait_ns, GramAcc<UT>& Gr,
+                                              GramAcc<UT>& Gi, VecAcc<UT>& Mr, VecAcc<UT>& Mn,
+                                              InstScale& sc) {
+  constexpr int NB = UT / 8, MT = WarpCfg<UT>::MT, S = WarpCfg<UT>::STAGES;
+#pragma unroll
+  for (int nt = 0; nt < NB; ++nt)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Mr[nt][k] = Mn[nt][k] = 0.f;
+#pragma unroll
+      for (int m = 0; m < MT; ++m) Gr[m][nt][k] = Gi[m][nt][k] = 0.f;
+    }
+  const int KS = (B + 7) / 8;
+  float2 h[MT][4], y[4];
+  tma_gram_issue<UT, true>(ring, tr, tmH, tmY, z, KS, S - 1);
+  bool ok = tma_gram_read<UT, true>(ring, tr, 0, wait_ns, h, y);
+  sc = scale_from_ks<UT>(h);
+  const float sh = pow2f(-sc.e()), sy0 = pow2f(-sc.f(0)), sy1 = pow2f(-sc.f(1));
+  for (int ks = 0;;) {
+    apply_scale<UT, true>(h, y, sh, sy0, sy1);
+    gram_ks<UT, EL, X3, true>(h, y, Gr, Gi, Mr, Mn);
+    if (++ks >= KS) break;
+    tma_gram_issue<UT, true>(ring, tr, tmH, tmY, z, KS, ks + S - 1);
+    ok &= tma_gram_read<UT, true>(ring, tr, ks, wait_ns, h, y);
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
 // x[0] *= s0, x[1] *= s1 (rows g and g + 8 of the lane).
 template <int NB>
 __device__ __forceinline__ void scale_rows(float2 (&x)[2][NB][2], float s0, float s1) {
@@ -1253,7 +1422,8 @@ __device__ __forceinline__ void scale_rows(float2 (&x)[2][NB][2], float s0, floa
       }
 }
 
-// Lines 7-19 and Eq. 4 of one instance whose Gram and matched filters are done.
+// The CG iterations, tracker and outputs of Algorithm 1 and Eq. 4 of one
+// instance whose Gram and matched filters are done.
 // Solvers of the warp bodies: CG (Algorithm 1) or the Neumann series (Sec. III-F).
 constexpr int SOLVE_CG = 0;
 constexpr int SOLVE_NEUMANN = 1;
@@ -1461,7 +1631,13 @@ __device__ __forceinline__ int64_t warp_next_early(const S& s, int64_t cur, int6
 
 // Instance loop: the Gram of an instance, then the next instance's first
 // load stages, then the CG and outputs (which overlap those loads).
-template <int UT, int EL, bool X3, class Src, int SOLVER = SOLVE_CG>
+//
+// TMA (DetectArgs of a __grid_constant__ kernel parameter only): when the
+// call carries tensor maps, the vector-layout instances stage their k-steps
+// through them instead of the lanes' cp.async copies. The mbarriers follow
+// the CTA's warp slices (WarpCfg::TMA_SMEM). A wait that runs out marks the
+// instance CG_STATUS_TIMEOUT and ends the warp's loop.
+template <int UT, int EL, bool X3, class Src, int SOLVER = SOLVE_CG, bool TMA = false>
 __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* mine) {
   constexpr int NB = UT / 8;
   const int warp = threadIdx.x >> 5;
@@ -1474,10 +1650,34 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
   // kLate: the next instance's first stages are issued after the finish,
   // which uses the ring as scratch (ExactStage)
   constexpr bool kLate = ExactStage<UT, SOLVER>::kOn;
+  TmaRing tr;
+  bool use_tma = false;
+  if constexpr (TMA) {
+    unsigned char* smem0 = mine - warp * WarpCfg<UT>::WARP_BYTES;
+    use_tma = src.tma != 0 && (smem_addr(smem0) & 1023u) == 0;
+    if (use_tma) {
+      tma_ring_init(tr, smem_addr(smem0) + WarpCfg<UT>::SMEM + 8 * warp * WarpCfg<UT>::STAGES,
+                    WarpCfg<UT>::STAGES);
+      if ((threadIdx.x & 31) == 0) {
+        tma_prefetch_map(&src.tmH);
+        tma_prefetch_map(&src.tmY);
+      }
+    }
+  }
+  // first k-steps of instance idx into the ring
+  auto prologue = [&](const DetItem& x, int64_t idx) {
+    if constexpr (TMA) {
+      if (use_tma) {
+        tma_gram_prologue<UT, true>(ring, tr, &src.tmH, &src.tmY, int(idx), x.B);
+        return;
+      }
+    }
+    ring_gram_prologue<UT, true>(ring, x.H, x.Y, x.B, x.R);
+  };
   if (cur >= 0) {
     const DetItem it = det_item(src, cur);
     vec = detect_vec<UT>(it);
-    if (vec) ring_gram_prologue<UT, true>(ring, it.H, it.Y, it.B, it.R);
+    if (vec) prologue(it, cur);
   }
   // An instance the fast path hands back (kRedo) runs once more with scales
   // from every entry and element loads (redo.w != 0), while the ring keeps
@@ -1494,12 +1694,27 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
     const bool again = redo.w != 0;
     {
       const DetItem it = det_item(src, cur);
-      if (vec && !again)
-        warp_gram<UT, EL, X3, LD_RING, true>(it.H, it.Y, it.B, it.U, it.R, ring, Gr, Gi, Mr, Mn,
-                                             sc, false);
-      else
+      bool landed = true;
+      if (vec && !again) {
+        if constexpr (TMA) {
+          if (use_tma)
+            landed = warp_gram_tma<UT, EL, X3>(it.B, ring, tr, &src.tmH, &src.tmY, int(cur),
+                                               src.wait_ns, Gr, Gi, Mr, Mn, sc);
+          else
+            warp_gram<UT, EL, X3, LD_RING, true>(it.H, it.Y, it.B, it.U, it.R, ring, Gr, Gi, Mr,
+                                                 Mn, sc, false);
+        } else {
+          warp_gram<UT, EL, X3, LD_RING, true>(it.H, it.Y, it.B, it.U, it.R, ring, Gr, Gi, Mr, Mn,
+                                               sc, false);
+        }
+      } else {
         warp_gram<UT, EL, X3, LD_ELEM, true>(it.H, it.Y, it.B, it.U, it.R, ring, Gr, Gi, Mr, Mn,
                                              sc, again);
+      }
+      if (!landed) {  // the inputs never arrived: report it and stop this warp
+        if ((threadIdx.x & 31) == 0 && it.status) *it.status = ST_TIMEOUT;
+        break;
+      }
     }
     if (!again) {
       next = warp_next_early(src, cur, nw);
@@ -1507,7 +1722,7 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
       if (next >= 0) {
         const DetItem nit = det_item(src, next);
         nvec = detect_vec<UT>(nit);
-        if (nvec && !kLate) ring_gram_prologue<UT, true>(ring, nit.H, nit.Y, nit.B, nit.R);
+        if (nvec && !kLate) prologue(nit, next);
       }
     }
     int st;
@@ -1529,7 +1744,7 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
       __syncwarp();  // every lane is done with the scratch
       if (next >= 0 && nvec) {
         const DetItem nit = det_item(src, next);
-        ring_gram_prologue<UT, true>(ring, nit.H, nit.Y, nit.B, nit.R);
+        prologue(nit, next);
       }
     }
     __syncwarp();
@@ -1540,7 +1755,7 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
         if (next >= 0) {
           const DetItem nit = det_item(src, next);
           nvec = detect_vec<UT>(nit);
-          if (nvec) ring_gram_prologue<UT, true>(ring, nit.H, nit.Y, nit.B, nit.R);
+          if (nvec) prologue(nit, next);
         }
       }
     }
@@ -1548,13 +1763,17 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
     vec = nvec;
   }
   cp_wait<0>();
+  if constexpr (TMA) {
+    if (use_tma) tma_ring_drain<UT>(tr);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // CG-P, one warp per instance
 // ---------------------------------------------------------------------------
 
-// Lines 7-14 with b = t, ||q||, then line 20 (q = H v) of one instance whose
+// The CG iterations of Algorithm 1 with b = t, ||q||, then the precoding
+// output q = H v (Sec. III-D) of one instance whose
 // Gram is done. hsc holds the scale e of H; each row of T gets its own f
 // here: the CG runs on 2^-e H, 2^-f t and 2^-2e sigma, giving v' = 2^(2e - f) v,
 // and q = 2^(f - e) (2^-e H) v', ||q|| = 2^(f - e) ||2^-e H v'||. With CHECK
@@ -1643,7 +1862,7 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
   const float hsh = pow2f(-sc.e());  // H' = 2^-e H in the second pass too
   const bool hscaled = sc.e() != 0;
 
-  // ---- line 20: q = H v on the tensor cores, 8 antennas per n-tile
+  // ---- precoding output q = H v on the tensor cores, 8 antennas per n-tile
   uint32_t vh[NB][4], vl[NB][4];
 #pragma unroll
   for (int ks = 0; ks < NB; ++ks) {
@@ -1799,8 +2018,9 @@ __device__ __forceinline__ unsigned char* warp_slice() {
 }
 
 template <int UT, int EL, bool X3>
-__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, WarpCfg<UT>::MINB) detect_warp_kernel(const DetectArgs a) {
-  detect_warp_body<UT, EL, X3>(a, warp_slice<WarpCfg<UT>::WARP_BYTES>());
+__global__ void __launch_bounds__(WarpCfg<UT>::NTHR, WarpCfg<UT>::MINB)
+    detect_warp_kernel(const __grid_constant__ DetectArgs a) {
+  detect_warp_body<UT, EL, X3, DetectArgs, SOLVE_CG, true>(a, warp_slice<WarpCfg<UT>::WARP_BYTES>());
 }
 template <int UT, int EL, bool X3>
 __global__ void __launch_bounds__(WarpCfg<UT>::NTHR, WarpCfg<UT>::MINB) precode_warp_kernel(const PrecodeArgs a) {

@@ -51,7 +51,7 @@ int64_t warp_grid(int resident, int64_t n_units, int max_grid) {
 
 template <int UT, int EL, bool X3>
 cudaError_t det(const DetectArgs& a, cudaStream_t s) {
-  constexpr uint32_t smem = WarpCfg<UT>::SMEM;
+  constexpr uint32_t smem = WarpCfg<UT>::TMA_SMEM;
   int res = 0;
   const uint64_t id = 0x100 | (UT << 2) | (EL << 1) | (X3 ? 1 : 0);
   cudaError_t err = resident_ctas(detect_warp_kernel<UT, EL, X3>, id, smem, &res);
