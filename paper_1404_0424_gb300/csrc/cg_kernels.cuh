@@ -65,8 +65,6 @@ struct PrecodeArgs {
   int bulk_h;  // H may be fetched with bulk copies
   int bulk_t;  // T may be fetched with bulk copies
   uint64_t wait_ns;  // limit of the wait for an instance's bulk copies (cg_set_wait_limit)
-  int tma;         // tmH is valid (as in DetectArgs)
-  CUtensorMap tmH;
 };
 
 // Byte offsets into dynamic shared memory; computed identically on host and

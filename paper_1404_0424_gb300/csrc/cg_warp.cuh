@@ -205,7 +205,7 @@ __device__ __forceinline__ void ring_gram_prologue(unsigned char* ring, const fl
 // bytes, the span of the swizzle pattern.
 struct TmaRing {
   uint32_t bar;  // shared-space address of this warp's STAGES mbarriers (8 bytes apart)
-  uint32_t st;   // bits 0-7: parity of each slot's next phase; 8-15: slots in flight
+  uint32_t st;   // bits 0-15: parity of each slot's next phase; 16-31: slots in flight
 };
 
 __device__ __forceinline__ void tma_ring_init(TmaRing& tr, uint32_t bar, int stages) {
@@ -237,7 +237,7 @@ __device__ __forceinline__ void tma_gram_issue(unsigned char* ring, TmaRing& tr,
     for (int m = 0; m < MT; ++m) tma_load_3d_s(base + m * 1024, tmH, 32 * m, 8 * ks, z, bar);
     if constexpr (MF) tma_load_3d_s(base + MT * 1024, tmY, 16 * ks, 0, z, bar);
   }
-  tr.st |= 256u << slot;
+  tr.st |= 65536u << slot;
 }
 
 // First STAGES - 1 k-steps of instance z. The fence orders earlier generic
@@ -254,16 +254,21 @@ __device__ __forceinline__ void tma_gram_prologue(unsigned char* ring, TmaRing& 
 }
 
 // Waits for k-step ks (bounded by wait_ns) and reads the lane's fragments;
-// false if the wait ran out (the fragments are then not valid).
+// false (warp-uniform) if the wait ran out. The slot then stays marked in
+// flight with its phase pending, the fragments are not valid, and the
+// caller issues nothing more on this ring: a second arrival on a pending
+// phase, or a second copy into a slot still being written, is not allowed.
 template <int UT, bool MF>
 __device__ __forceinline__ bool tma_gram_read(unsigned char* ring, TmaRing& tr, int ks,
                                               uint64_t wait_ns,
                                               float2 (&h)[WarpCfg<UT>::MT][4], float2 (&y)[4]) {
   constexpr int MT = WarpCfg<UT>::MT, PL = WarpCfg<UT>::PLANES;
   const int slot = ks % WarpCfg<UT>::STAGES;
-  const bool ok = mbar_wait_bounded_s(tr.bar + 8 * slot, (tr.st >> slot) & 1u, wait_ns);
+  const bool ok = __all_sync(
+      0xffffffffu, mbar_wait_bounded_s(tr.bar + 8 * slot, (tr.st >> slot) & 1u, wait_ns));
+  if (!ok) return false;
   tr.st ^= 1u << slot;
-  tr.st &= ~(256u << slot);
+  tr.st &= ~(65536u << slot);
   const unsigned char* base = ring + slot * PL * 512;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int r0 = 2 * t, r1 = 2 * t + 1;
@@ -294,20 +299,20 @@ __device__ __forceinline__ bool tma_gram_read(unsigned char* ring, TmaRing& tr, 
     y[1] = make_float2(w1.x, w1.y);
     y[3] = make_float2(w1.z, w1.w);
   }
-  return ok;
+  return true;
 }
 
 // Waits (bounded) for every slot still in flight, so that no copy lands in
-// shared memory after the warp is done with it.
-template <int UT>
-__device__ __forceinline__ void tma_ring_drain(TmaRing& tr) {
+// shared memory after the warp is done with it. Each such slot has exactly
+// one pending phase, the one its parity bit names.
+__device__ __forceinline__ void tma_ring_drain(TmaRing& tr, int stages) {
 #pragma unroll 1
-  for (int slot = 0; slot < WarpCfg<UT>::STAGES; ++slot)
-    if ((tr.st >> (8 + slot)) & 1u) {
+  for (int slot = 0; slot < stages; ++slot)
+    if ((tr.st >> (16 + slot)) & 1u) {
       mbar_wait_bounded_s(tr.bar + 8 * slot, (tr.st >> slot) & 1u, WAIT_TIMEOUT_NS);
       tr.st ^= 1u << slot;
     }
-  tr.st &= 255u;
+  tr.st &= 65535u;
 }
 
 // Prefetch into L1 of the 8-antenna block ks of an instance's H with UT
@@ -327,6 +332,14 @@ __device__ __forceinline__ void prefetch_h_block(const float2* H, int B, int ks)
       asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
     }
   }
+}
+// Prefetch into L1 of `bytes` contiguous bytes from p (16-byte aligned),
+// one 128-byte line per lane; only lines that start inside the range.
+__device__ __forceinline__ void prefetch_rows_l1(const void* p, int bytes) {
+  const char* c = reinterpret_cast<const char*>(p);
+  const int base = int(reinterpret_cast<uintptr_t>(c) & 127);
+  for (int off = (threadIdx.x & 31) * 128 - base; off < bytes; off += 32 * 128)
+    if (off + 128 > 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(c + (off < 0 ? 0 : off)));
 }
 #ifndef CGM_PF_GRAM
 #define CGM_PF_GRAM 4  // blocks ahead in the Gram pass of the 16-byte path
@@ -1395,7 +1408,7 @@ __device__ __forceinline__ bool warp_gram_tma(int B, unsigned char* ring, TmaRin
   const int KS = (B + 7) / 8;
   float2 h[MT][4], y[4];
   tma_gram_issue<UT, true>(ring, tr, tmH, tmY, z, KS, S - 1);
-  bool ok = tma_gram_read<UT, true>(ring, tr, 0, wait_ns, h, y);
+  if (!tma_gram_read<UT, true>(ring, tr, 0, wait_ns, h, y)) return false;
   sc = scale_from_ks<UT>(h);
   const float sh = pow2f(-sc.e()), sy0 = pow2f(-sc.f(0)), sy1 = pow2f(-sc.f(1));
   for (int ks = 0;;) {
@@ -1403,9 +1416,9 @@ __device__ __forceinline__ bool warp_gram_tma(int B, unsigned char* ring, TmaRin
     gram_ks<UT, EL, X3, true>(h, y, Gr, Gi, Mr, Mn);
     if (++ks >= KS) break;
     tma_gram_issue<UT, true>(ring, tr, tmH, tmY, z, KS, ks + S - 1);
-    ok &= tma_gram_read<UT, true>(ring, tr, ks, wait_ns, h, y);
+    if (!tma_gram_read<UT, true>(ring, tr, ks, wait_ns, h, y)) return false;
   }
-  return __all_sync(0xffffffffu, ok);
+  return true;
 }
 
 // x[0] *= s0, x[1] *= s1 (rows g and g + 8 of the lane).
@@ -1764,7 +1777,7 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
   }
   cp_wait<0>();
   if constexpr (TMA) {
-    if (use_tma) tma_ring_drain<UT>(tr);
+    if (use_tma) tma_ring_drain(tr, WarpCfg<UT>::STAGES);
   }
 }
 
@@ -1779,10 +1792,13 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
 // and q = 2^(f - e) (2^-e H) v', ||q|| = 2^(f - e) ||2^-e H v'||. With CHECK
 // (the fast path), an instance whose scaled Gram lies outside the range the
 // FP16 split needs returns kRedo before anything is stored.
+// nit, when given, is the warp's next instance: the first blocks of its H
+// and its T are prefetched into L1 while this q pass runs.
 template <int UT, int EL, bool X3, bool VEC, int SOLVER = SOLVE_CG>
 __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* frag,
                                                    const GramAcc<UT>& Gr, const GramAcc<UT>& Gi,
-                                                   InstScale hsc, bool check) {
+                                                   InstScale hsc, bool check,
+                                                   const PreItem* nit = nullptr) {
   constexpr int NB = UT / 8;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   WarpCg<UT, EL> cg;
@@ -1884,6 +1900,11 @@ __device__ __forceinline__ int precode_warp_finish(const PreItem& it, uint2* fra
 #pragma unroll
     for (int d = 1; d <= PF_Q; ++d) prefetch_h_block<UT>(it.H, it.B, d);
     q_load<UT>(it.H, it.B, 0, g, t, fa);
+    if (nit != nullptr) {
+#pragma unroll
+      for (int d = 0; d <= PF_GRAM; ++d) prefetch_h_block<UT>(nit->H, nit->B, d);
+      prefetch_rows_l1(nit->T, nit->R * nit->U * 8);
+    }
   }
   for (int nb = 0; nb < NBQ; ++nb) {
     if constexpr (VEC) prefetch_h_block<UT>(it.H, it.B, nb + 1 + PF_Q);
@@ -1987,7 +2008,12 @@ __device__ __forceinline__ void precode_warp_body(const Src& src, unsigned char*
     if (precode_vec<UT>(it)) {
       warp_gram<UT, EL, X3, LD_VEC, false>(it.H, nullptr, it.B, it.U, 0, nullptr, Gr, Gi, Mr, Mn,
                                            sc, again);
-      st = precode_warp_finish<UT, EL, X3, true, SOLVER>(it, frag, Gr, Gi, sc, !again);
+      int64_t nx = -1;
+      if constexpr (!SrcTraits<Src>::kDyn) nx = warp_next_early(src, cur, nw);
+      PreItem nit;
+      if (nx >= 0) nit = pre_item(src, nx);
+      st = precode_warp_finish<UT, EL, X3, true, SOLVER>(it, frag, Gr, Gi, sc, !again,
+                                                         nx >= 0 ? &nit : nullptr);
     } else {
       warp_gram<UT, EL, X3, LD_ELEM, false>(it.H, nullptr, it.B, it.U, 0, nullptr, Gr, Gi, Mr,
                                             Mn, sc, again);

@@ -1,7 +1,8 @@
-"""The bounded device wait of the FP32 kernels and CG_STATUS_TIMEOUT.
+"""The bounded device waits for input copies and CG_STATUS_TIMEOUT.
 
 The FP32 kernels fetch each instance's inputs with bulk copies into shared
-memory and wait for them on an mbarrier for a bounded time. With the limit
+memory, and CG-D's split-precision warp kernels stage H and Y with tensor
+copies; both wait for them on mbarriers for a bounded time. With the limit
 set to 1 ns (cg_set_wait_limit) the copies of a CTA's first instance cannot
 land in time: that CTA reports CG_STATUS_TIMEOUT, lets its copies in flight
 land and stops, and the call completes without a fault. The next call, with
@@ -87,3 +88,35 @@ def test_precode_wait_runs_out_then_recovers(cabi):
     torch.cuda.synchronize()
     check_precode({k: to_np(v) for k, v in out.items()},
                   oracle.cg_precode(d["H"][:32], d["T"][:32], d["N0"], 1.0, 3))
+
+
+def test_tma_wait_runs_out_then_recovers(cabi):
+    """CG-D single calls in the split precisions stage H and Y with tensor
+    copies (TMA) on mbarriers, waited for with the same bounded wait: at a
+    1 ns limit a warp's first wait runs out, that instance reports
+    CG_STATUS_TIMEOUT, and the warp issues nothing more and stops once its
+    copies in flight have landed."""
+    dev = torch.device("cuda:0")
+    n = 4096
+    d = wl.uplink(128, 16, 6, n=n, R=14, snr_db=10.0, seed=45)
+    H = torch.from_numpy(d["H"]).to(dev)
+    Y = torch.from_numpy(d["Y"]).to(dev)
+    outs = (torch.zeros((n, 14, 16), dtype=torch.complex64, device=dev),
+            torch.zeros((n, 14, 16), device=dev), torch.zeros((n, 14, 16), device=dev),
+            torch.zeros((n, 14, 16, 6), device=dev))
+    st = torch.full((n,), -1, dtype=torch.int32, device=dev)
+    p = cabi.params(128, 16, 6, 3, 14, d["N0"], precision=4)
+    assert cabi.cg_set_wait_limit(1) == cabi.CG_OK
+    try:
+        assert cabi.cg_detect(p, n, H, Y, *outs, st) == cabi.CG_OK
+        torch.cuda.synchronize()
+    finally:
+        assert cabi.cg_set_wait_limit(0) == cabi.CG_OK
+    s, timed_out = _timed_out(cabi, st)
+    assert timed_out.any(), "no instance reported CG_STATUS_TIMEOUT"
+    assert np.all((s == -1) | timed_out | ((s >= 0) & (s <= 3)))
+    # the context is still usable and the default limit gives the normal results
+    out = cabi.detect(H[:64], Y[:64], d["N0"], 3, 6, precision=4)
+    torch.cuda.synchronize()
+    check_detect({k: to_np(v) for k, v in out.items()},
+                 oracle.cg_detect(d["H"][:64], d["Y"][:64], d["N0"], 1.0, 3, 6))
