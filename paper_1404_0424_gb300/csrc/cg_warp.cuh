@@ -31,6 +31,9 @@
 
 #include "cg_tc.cuh"
 
+#ifndef CGM_WARP_MINB32
+#define CGM_WARP_MINB32 2  // resident CTAs per SM the register allocation targets at 32 users
+#endif
 #ifndef CGM_WARP_MINB
 #define CGM_WARP_MINB 3  // resident CTAs per SM the register allocation targets at 16 users
 #endif
@@ -62,7 +65,7 @@ struct WarpCfg {
   static constexpr int NTHR = 32 * WARPS;
   // resident CTAs per SM targeted: 8 users fit 4 CTAs in 128 registers; 16
   // users run faster at 3 CTAs without spills than at 4 with them
-  static constexpr int MINB = UT == 32 ? 2 : UT == 16 ? CGM_WARP_MINB : 4;
+  static constexpr int MINB = UT == 32 ? CGM_WARP_MINB32 : UT == 16 ? CGM_WARP_MINB : 4;
   // per warp: a ring of STAGES load stages (PLANES planes of 16 bytes
   // per lane each), the CG B fragments (one uint2 per lane and fragment), and
   // alpha_k, beta_k of the 16 right-hand-side rows for the tracker (K <= UT)
@@ -220,14 +223,14 @@ __device__ __forceinline__ void tma_ring_init(TmaRing& tr, uint32_t bar, int sta
 
 // Issues k-step ks (< KS) of instance z into its slot. Every lane has read
 // the slot's previous contents into registers before the __syncwarp.
-template <int UT, bool MF>
+template <int UT, bool MF, int S = WarpCfg<UT>::STAGES>
 __device__ __forceinline__ void tma_gram_issue(unsigned char* ring, TmaRing& tr,
                                                const CUtensorMap* tmH, const CUtensorMap* tmY,
                                                int z, int KS, int ks) {
   if (ks >= KS) return;
   constexpr int MT = WarpCfg<UT>::MT, PL = WarpCfg<UT>::PLANES;
   constexpr uint32_t HBOX = UT == 8 ? 512u : 1024u;
-  const int slot = ks % WarpCfg<UT>::STAGES;
+  const int slot = ks % S;
   __syncwarp();
   if ((threadIdx.x & 31) == 0) {
     const uint32_t base = smem_addr(ring) + slot * PL * 512;
@@ -240,17 +243,16 @@ __device__ __forceinline__ void tma_gram_issue(unsigned char* ring, TmaRing& tr,
   tr.st |= 65536u << slot;
 }
 
-// First STAGES - 1 k-steps of instance z. The fence orders earlier generic
-// writes to the ring (scratch) before the tensor copies that overwrite it.
-template <int UT, bool MF>
+// First S - 1 k-steps ks0, ks0 + 1, ... (below KS) of instance z. The fence
+// orders earlier generic writes to the ring (scratch) before the tensor
+// copies that overwrite it.
+template <int UT, bool MF, int S = WarpCfg<UT>::STAGES>
 __device__ __forceinline__ void tma_gram_prologue(unsigned char* ring, TmaRing& tr,
                                                   const CUtensorMap* tmH, const CUtensorMap* tmY,
-                                                  int z, int B) {
-  const int KS = (B + 7) / 8;
+                                                  int z, int KS, int ks0 = 0) {
   fence_proxy_async_smem();
 #pragma unroll
-  for (int ks = 0; ks < WarpCfg<UT>::STAGES - 1; ++ks)
-    tma_gram_issue<UT, MF>(ring, tr, tmH, tmY, z, KS, ks);
+  for (int i = 0; i < S - 1; ++i) tma_gram_issue<UT, MF, S>(ring, tr, tmH, tmY, z, KS, ks0 + i);
 }
 
 // Waits for k-step ks (bounded by wait_ns) and reads the lane's fragments;
@@ -258,12 +260,12 @@ __device__ __forceinline__ void tma_gram_prologue(unsigned char* ring, TmaRing& 
 // flight with its phase pending, the fragments are not valid, and the
 // caller issues nothing more on this ring: a second arrival on a pending
 // phase, or a second copy into a slot still being written, is not allowed.
-template <int UT, bool MF>
+template <int UT, bool MF, int S = WarpCfg<UT>::STAGES>
 __device__ __forceinline__ bool tma_gram_read(unsigned char* ring, TmaRing& tr, int ks,
                                               uint64_t wait_ns,
                                               float2 (&h)[WarpCfg<UT>::MT][4], float2 (&y)[4]) {
   constexpr int MT = WarpCfg<UT>::MT, PL = WarpCfg<UT>::PLANES;
-  const int slot = ks % WarpCfg<UT>::STAGES;
+  const int slot = ks % S;
   const bool ok = __all_sync(
       0xffffffffu, mbar_wait_bounded_s(tr.bar + 8 * slot, (tr.st >> slot) & 1u, wait_ns));
   if (!ok) return false;
@@ -1214,6 +1216,66 @@ __device__ __forceinline__ void axis_llr_gray(float u, float scale, float (&out)
   }
 }
 
+// x_hat, mu, rho and the max-log LLRs (Eq. 4) of NUG users u0 .. u0 + NUG - 1
+// of right-hand-side row r (users past U skipped unless VEC: contiguous
+// users, 16-byte aligned rows).
+template <int NUG, int QB, bool VEC>
+__device__ __forceinline__ void store_users_detect(const DetItem& it, int r, int u0,
+                                                   const float2 (&xo)[NUG], const float (&mo)[NUG],
+                                                   const float (&ro)[NUG], float cq, int* flags) {
+  constexpr int H = QB / 2;
+  const int64_t base = int64_t(r) * it.U + u0;
+  if constexpr (VEC) {
+    if (it.xhat) {
+      float4* xp = reinterpret_cast<float4*>(it.xhat + base);
+#pragma unroll
+      for (int m = 0; m < NUG; m += 2)
+        xp[m / 2] = make_float4(xo[m].x, xo[m].y, xo[m + 1].x, xo[m + 1].y);
+    }
+    if constexpr (NUG == 4) {
+      if (it.mu)
+        *reinterpret_cast<float4*>(it.mu + base) = make_float4(mo[0], mo[1], mo[2], mo[3]);
+      if (it.rho)
+        *reinterpret_cast<float4*>(it.rho + base) = make_float4(ro[0], ro[1], ro[2], ro[3]);
+    } else {
+      if (it.mu) *reinterpret_cast<float2*>(it.mu + base) = make_float2(mo[0], mo[1]);
+      if (it.rho) *reinterpret_cast<float2*>(it.rho + base) = make_float2(ro[0], ro[1]);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NUG; ++m) {
+    const bool in = VEC || u0 + m < it.U;
+    if (!in) continue;
+    const bool valid = mo[m] > 0.f;
+    if (!valid) *flags |= ST_MU_NONPOS;
+    const int64_t o = base + m;
+    if constexpr (!VEC) {
+      if (it.xhat) it.xhat[o] = xo[m];
+      if (it.mu) it.mu[o] = mo[m];
+      if (it.rho) it.rho[o] = ro[m];
+    }
+    if (it.llr) {
+      float lI[H], lQ[H];
+      if (valid) {
+        const float inv = __frcp_rn(mo[m] * cq);  // u = x_hat / (mu c)
+        const float scale = ro[m] * cq * cq;
+        axis_llr_gray<H>(xo[m].x * inv, scale, lI);
+        axis_llr_gray<H>(xo[m].y * inv, scale, lQ);
+      } else {
+#pragma unroll
+        for (int k = 0; k < H; ++k) lI[k] = lQ[k] = 0.f;
+      }
+      float2* lp = reinterpret_cast<float2*>(it.llr + o * QB);
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        const float a = 2 * k < H ? lI[2 * k] : lQ[2 * k - H];
+        const float b = 2 * k + 1 < H ? lI[2 * k + 1] : lQ[2 * k + 1 - H];
+        lp[k] = make_float2(a, b);
+      }
+    }
+  }
+}
+
 // The 2 NB users of a lane in one right-hand-side row, in memory order
 // (16 users: 4t + m holds position (nt, c) = (m & 1, m >> 1); 8 users:
 // 2t + m holds (0, m)). VEC: contiguous users, 16-byte aligned rows.
@@ -1223,12 +1285,11 @@ __device__ __forceinline__ void store_row_detect(const DetItem& it, int r, int t
                                                  const float (&mu)[UT / 8][2],
                                                  const float (&rho)[UT / 8][2], float cq,
                                                  int* flags) {
-  constexpr int MT = WarpCfg<UT>::MT, NUG = UT == 8 ? 2 : 4, H = QB / 2;
+  constexpr int MT = WarpCfg<UT>::MT, NUG = UT == 8 ? 2 : 4;
 #pragma unroll
   for (int gr = 0; gr < MT; ++gr) {
     // users 16 gr + 4t + m (m = 2c + nt % 2, nt = 2 gr + m % 2), or 2t + m
     const int u0 = UT == 8 ? 2 * t : 16 * gr + 4 * t;
-    const int64_t base = int64_t(r) * it.U + u0;
     float2 xo[NUG];
     float mo[NUG], ro[NUG];
 #pragma unroll
@@ -1238,55 +1299,7 @@ __device__ __forceinline__ void store_row_detect(const DetItem& it, int r, int t
       mo[m] = mu[nt][c];
       ro[m] = rho[nt][c];
     }
-    if constexpr (VEC) {
-      if (it.xhat) {
-        float4* xp = reinterpret_cast<float4*>(it.xhat + base);
-#pragma unroll
-        for (int m = 0; m < NUG; m += 2)
-          xp[m / 2] = make_float4(xo[m].x, xo[m].y, xo[m + 1].x, xo[m + 1].y);
-      }
-      if constexpr (NUG == 4) {
-        if (it.mu)
-          *reinterpret_cast<float4*>(it.mu + base) = make_float4(mo[0], mo[1], mo[2], mo[3]);
-        if (it.rho)
-          *reinterpret_cast<float4*>(it.rho + base) = make_float4(ro[0], ro[1], ro[2], ro[3]);
-      } else {
-        if (it.mu) *reinterpret_cast<float2*>(it.mu + base) = make_float2(mo[0], mo[1]);
-        if (it.rho) *reinterpret_cast<float2*>(it.rho + base) = make_float2(ro[0], ro[1]);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < NUG; ++m) {
-      const bool in = VEC || u0 + m < it.U;
-      if (!in) continue;
-      const bool valid = mo[m] > 0.f;
-      if (!valid) *flags |= ST_MU_NONPOS;
-      const int64_t o = base + m;
-      if constexpr (!VEC) {
-        if (it.xhat) it.xhat[o] = xo[m];
-        if (it.mu) it.mu[o] = mo[m];
-        if (it.rho) it.rho[o] = ro[m];
-      }
-      if (it.llr) {
-        float lI[H], lQ[H];
-        if (valid) {
-          const float inv = __frcp_rn(mo[m] * cq);  // u = x_hat / (mu c)
-          const float scale = ro[m] * cq * cq;
-          axis_llr_gray<H>(xo[m].x * inv, scale, lI);
-          axis_llr_gray<H>(xo[m].y * inv, scale, lQ);
-        } else {
-#pragma unroll
-          for (int k = 0; k < H; ++k) lI[k] = lQ[k] = 0.f;
-        }
-        float2* lp = reinterpret_cast<float2*>(it.llr + o * QB);
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-          const float a = 2 * k < H ? lI[2 * k] : lQ[2 * k - H];
-          const float b = 2 * k + 1 < H ? lI[2 * k + 1] : lQ[2 * k + 1 - H];
-          lp[k] = make_float2(a, b);
-        }
-      }
-    }
+    store_users_detect<NUG, QB, VEC>(it, r, u0, xo, mo, ro, cq, flags);
   }
 }
 
@@ -1681,7 +1694,7 @@ __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* 
   auto prologue = [&](const DetItem& x, int64_t idx) {
     if constexpr (TMA) {
       if (use_tma) {
-        tma_gram_prologue<UT, true>(ring, tr, &src.tmH, &src.tmY, int(idx), x.B);
+        tma_gram_prologue<UT, true>(ring, tr, &src.tmH, &src.tmY, int(idx), (x.B + 7) / 8);
         return;
       }
     }
