@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--slots", type=int, default=32, help="1200x14 slots per step")
+    ap.add_argument("--B", type=int, default=B, help="antennas (profiling runs of other shapes)")
     ap.add_argument("--U", type=int, default=U)
+    ap.add_argument("--qam", type=int, default=QAM, help="bits per QAM symbol")
     ap.add_argument("--K", type=int, default=KITER)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -472,6 +474,7 @@ def run_ours(args):
 
     from paper_1404_0424_gb300 import build, cabi, shard, workload as wl
 
+    B, QAM = args.B, args.qam  # the workload's shape (defaults: the headline configuration)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -796,13 +799,14 @@ def run_ours(args):
         srv = serving or {}
         low = srv.get("low_load", {})
         line = {
-            "metric": "CG solves/s (detect + precode) at B=128, U=16, 64-QAM, R=14, K=3",
+            "metric": f"CG solves/s (detect + precode) at B={B}, U={Un}, {1 << QAM}-QAM, R={R}, "
+                      f"K={K}",
             "value": round(value, 1), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision],
             "data": "synthetic (seeded i.i.d. CN(0,1) channels, Gray 64-QAM, AWGN at 10 dB)",
-            "config": {"workload": f"uplink CG-D + downlink CG-P, B={B}, U={Un}, 64-QAM, "
+            "config": {"workload": f"uplink CG-D + downlink CG-P, B={B}, U={Un}, {1 << QAM}-QAM, "
                                    f"{NSC} subcarriers x {R} symbols per slot, K={K}, "
                                    f"SNR {SNR_DB} dB",
                        "precision": args.precision,
