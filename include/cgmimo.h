@@ -64,8 +64,9 @@ extern "C" {
 /* Per-instance status bits. */
 #define CG_STATUS_BREAKDOWN 1  /* CG stopped before K: ||r_{k-1}||^2 or Re(p^H A p) not > 0 */
 #define CG_STATUS_MU_NONPOS 2  /* some mu_{i|K} <= 0: that user's LLRs are set to 0 */
-#define CG_STATUS_TIMEOUT 4    /* an input copy did not complete in time (FP32 kernels,
-                                  cg_set_wait_limit); outputs not written */
+#define CG_STATUS_TIMEOUT 4    /* an input copy did not complete in time (FP32 kernels
+                                  and TMA-staged CG-D, cg_set_wait_limit); outputs not
+                                  written */
 
 /* SINR tracker (Sec. III-C). */
 #define CG_SINR_APPROX 0  /* Eqs. 11-13: diagonal recursion, rho = G_ii / N0 */
@@ -397,24 +398,27 @@ int cg_serve_destroy(cg_server* s);
  *
  * Each call looks up the device address of the static array on the
  * current device (make the device current first); the first call on a
- * device may load the library's device code, so make it before any stream
- * capture. Every call reuses the same array, which keeps the previous
+ * device may load the library's device code, so make one call ahead of
+ * deadline-bound use. Every call reuses the same array, which keeps the previous
  * call's contents; the call resets the parts that must start at zero.
  * Calls whose work overlaps on the GPU (different streams, or other
  * threads) race on the array: order them on one stream. */
 int cg_batch_run_static(const cg_desc* descs, int64_t n, int32_t precision, void* stream);
 
-/* Limit on the device-side wait of the FP32 kernels (CG_PREC_FP32, and the
- * implicit and CGLS modes) for an instance's inputs, which they fetch with
- * bulk copies into shared memory: after timeout_ns nanoseconds of GPU time
- * without the copies landing, the instance's status gets CG_STATUS_TIMEOUT,
- * its CTA waits (at most 2 s) for the copies still in flight and stops, and
- * the call completes without a fault; the remaining instances of that CTA
- * are left unwritten. 0 restores the default of 2 s; the limit applies to
- * calls made after it is set, in every thread. The paper has no counterpart:
- * it exists so that the timeout path can be exercised. Returns CG_EINVAL
- * outside [0, 60 s]. The tensor-core kernels stage their inputs with copies
- * that always complete and have no such wait. */
+/* Limit on the device-side waits for an instance's inputs: those of the
+ * FP32 kernels (CG_PREC_FP32, and the implicit and CGLS modes), which fetch
+ * them with bulk copies into shared memory, and those of CG-D single calls
+ * in the tensor-core precisions, which stage H and Y with tensor-map copies
+ * (TMA). After timeout_ns nanoseconds of GPU time without the copies
+ * landing, the instance's status gets CG_STATUS_TIMEOUT, its CTA (FP32) or
+ * warp (TMA) issues nothing more, waits (at most 2 s) for the copies still
+ * in flight and stops, and the call completes without a fault; the
+ * remaining instances of that CTA or warp are left unwritten. 0 restores
+ * the default of 2 s; the limit applies to calls made after it is set, in
+ * every thread. The paper has no counterpart: it exists so that the timeout
+ * path can be exercised. Returns CG_EINVAL outside [0, 60 s]. The other
+ * tensor-core paths stage their inputs with copies that always complete and
+ * have no such wait. */
 int cg_set_wait_limit(int64_t timeout_ns);
 
 /* Frees the workspace of the *_host calls on the current device. */
