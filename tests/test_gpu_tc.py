@@ -189,3 +189,22 @@ def test_bench_launch_38400_instances_sampled(cabi):
                   oracle.cg_precode(H, T[idx].cpu().numpy(), d["N0"], 1.0, 3))
     del d, out, pre, T
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("mode", list(X3))
+@pytest.mark.parametrize("B,U,R,K,q,n", [
+    (100, 16, 14, 3, 6, 7),   # ragged last k-step: rows 100..103 of its H box and Y box past B
+    (36, 8, 5, 2, 4, 5),      # 8 users: 64-byte swizzled H boxes, ragged last k-step
+    (8, 8, 16, 4, 2, 3),      # a single k-step (at K = U a square H leaves FP32 CG, on any
+                              # hardware, 1e-2 away from FP64: its last steps divide
+                              # vanishing residuals)
+    (18, 16, 3, 4, 4, 9),     # three k-steps, the last with 2 of 8 antennas
+    (250, 32, 7, 8, 8, 3),    # 32 users: two H boxes per k-step, ragged last k-step
+    (128, 16, 1, 3, 6, 1)])   # one instance, one right-hand side (Y box rows 1..15 past R)
+def test_detect_tma_staging_edges(cabi, mode, B, U, R, K, q, n):
+    """CG-D single calls with U equal to the padded user count, B even and
+    16-byte aligned buffers stage through tensor-map copies, which deliver
+    zeros for rows past B (H), antennas past B and rows past R (Y)."""
+    d = wl.uplink(B, U, q, n=n, R=R, snr_db=12.0, seed=B * 10 + U + R)
+    check_detect(run(cabi, d, K, X3[mode]),
+                 oracle.cg_detect(d["H"], d["Y"], d["N0"], 1.0, K, q))
