@@ -218,3 +218,83 @@ def test_autotuner_times_then_caches_schedules(cabi, tmp_path):
         assert s3["source"] == cabi.CG_TUNE_FIXED and s3["precision"] == 4
     finally:
         cabi.cg_plan_destroy(plan3)
+
+
+def test_cached_schedule_decides(cabi, tmp_path):
+    """An entry of the schedule cache, edited and loaded back, is the schedule
+    the next plan of that shape class runs (source CACHED), and its results
+    still equal the single calls."""
+    import json
+    dev = torch.device("cuda:0")
+    probs = make_batch(24, seed=31, dev=dev, exact_every=11)
+    ds = descs(cabi, probs)
+    rc, plan, _ = cabi.cg_plan_create(ds, -1)
+    assert rc == 0
+    _, s1 = cabi.cg_plan_schedule(plan)
+    cabi.cg_plan_destroy(plan)
+    path = tmp_path / "tune.json"
+    assert cabi.cg_tune_cache_save(str(path)) >= 1
+    entries = json.loads(path.read_text())
+    # the entry timed just now: the one whose fields equal the plan's schedule
+    mine = [e for e in entries if all(e[f] == s1[f] for f in
+                                      ("precision", "order", "concurrent", "grid_pct"))]
+    assert mine
+    want = {"precision": 3 if s1["precision"] == 4 else 4, "order": 1 - s1["order"],
+            "concurrent": 1 - s1["concurrent"], "grid_pct": 50}
+    for e in mine:
+        e.update(want)
+    path.write_text("[\n" + ",\n".join(json.dumps(e) for e in mine) + "\n]\n")
+    assert cabi.cg_tune_cache_load(str(path)) == len(mine)
+    rc, plan2, _ = cabi.cg_plan_create(ds, -1)
+    assert rc == 0
+    try:
+        _, s2 = cabi.cg_plan_schedule(plan2)
+        assert s2["source"] == cabi.CG_TUNE_CACHED
+        assert all(s2[f] == want[f] for f in want), (s2, want)
+        assert cabi.cg_plan_run(plan2) == 0
+        torch.cuda.synchronize()
+        for p in probs:
+            ref = single(cabi, p, s2["precision"])
+            torch.cuda.synchronize()
+            keys = ("xhat", "mu", "rho", "llr", "status") if p["op"] == 0 else ("q", "qnorm",
+                                                                               "status")
+            for k in keys:
+                assert torch.equal(p["t"][k], ref[k]), f"{k} differs from the single call"
+    finally:
+        cabi.cg_plan_destroy(plan2)
+
+
+_CHILD = r"""
+import sys, torch
+sys.path.insert(0, {root!r})
+from tests.test_gpu_batched import make_batch, descs
+from paper_1404_0424_gb300 import build, cabi
+cabi.library(build.build())
+probs = make_batch(20, seed=41, dev=torch.device("cuda:0"), exact_every=13)
+rc, plan, _ = cabi.cg_plan_create(descs(cabi, probs), -1)
+assert rc == 0
+_, s = cabi.cg_plan_schedule(plan)
+cabi.cg_plan_destroy(plan)
+print(s["source"], s["precision"], s["order"], s["concurrent"], s["grid_pct"])
+"""
+
+
+def test_schedule_cache_file_across_processes(cabi, tmp_path):
+    """With CGMIMO_TUNE_CACHE naming a file, a schedule timed in one process
+    is taken from the file by the next process (source CACHED)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CGMIMO_TUNE_CACHE=str(tmp_path / "cache.json"))
+    code = _CHILD.format(root=root)
+    outs = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=600, cwd=root)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(r.stdout.split())
+    assert int(outs[0][0]) == cabi.CG_TUNE_TIMED
+    assert int(outs[1][0]) == cabi.CG_TUNE_CACHED
+    assert outs[0][1:] == outs[1][1:]
+    assert (tmp_path / "cache.json").exists()
