@@ -130,6 +130,19 @@ __device__ __forceinline__ unsigned long long load_acquire_sys(const unsigned lo
   return v;
 }
 
+// Relaxed loads of mapped host memory that do not depend on one another are
+// in flight together; a fence.acq_rel.sys after them gives them acquire
+// ordering for the loads that follow (one round trip to host memory for the
+// lot instead of one each).
+__device__ __forceinline__ unsigned long long load_relaxed_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel_sys() {
+  asm volatile("fence.acq_rel.sys;" ::: "memory");
+}
+
 // True when tag a belongs to an earlier request than tag b.
 __device__ __forceinline__ bool tag_older(unsigned long long a, unsigned long long b) {
   return int32_t(uint32_t(a) - uint32_t(b)) < 0;
@@ -169,9 +182,14 @@ __device__ __forceinline__ void copy_words_volatile(T* dst, const T* src) {
   static_assert(sizeof(T) % 8 == 0, "copied in 8-byte words");
   const unsigned long long* a = reinterpret_cast<const unsigned long long*>(src);
   unsigned long long* b = reinterpret_cast<unsigned long long*>(dst);
+  constexpr int NW = int(sizeof(T) / 8);
+  // every word's load first, so that they travel together (a source in
+  // mapped host memory costs one round trip for the lot, not one per word)
+  unsigned long long w[NW];
 #pragma unroll
-  for (int k = 0; k < int(sizeof(T) / 8); ++k)
-    *const_cast<volatile unsigned long long*>(b + k) = volatile_load(a + k);
+  for (int k = 0; k < NW; ++k) w[k] = volatile_load(a + k);
+#pragma unroll
+  for (int k = 0; k < NW; ++k) *const_cast<volatile unsigned long long*>(b + k) = w[k];
 }
 
 // The device copy of the request at sequence number `head` of the class, once
@@ -442,15 +460,25 @@ __device__ __forceinline__ int serve_pick(const ServeArgs& s, int home) {
 // host memory sees a few reads per microsecond, not one per warp, and the
 // warps' claims never read it.
 __device__ __forceinline__ void serve_poll_host(const ServeArgs& s) {
-  if (volatile_load(&s.ctrl->stop)) {
+  // the stop flag and the total travel together; the class tails, read
+  // after the total's acquire, are at least as new as it implies and travel
+  // together too; the fence then orders the entries and descriptors read
+  // after them
+  const int stop = volatile_load(&s.ctrl->stop);
+  const unsigned long long total = load_acquire_sys(&s.ctrl->class_tail[kServeTotal]);
+  if (stop) {
     *const_cast<volatile unsigned long long*>(&s.class_head[kServeStop]) = 1ull;
     return;
   }
-  const unsigned long long total = load_acquire_sys(&s.ctrl->class_tail[kServeTotal]);
   if (total <= volatile_load(&s.class_head[kServeTotal])) return;
+  unsigned long long tails[kWarpClasses];
+#pragma unroll
+  for (int c = 0; c < kWarpClasses; ++c) tails[c] = load_relaxed_sys(&s.ctrl->class_tail[c]);
+  fence_acq_rel_sys();
   bool all = true;
+#pragma unroll
   for (int c = 0; c < kWarpClasses; ++c) {
-    const unsigned long long tail = load_acquire_sys(&s.ctrl->class_tail[c]);
+    const unsigned long long tail = tails[c];
     const unsigned long long head = volatile_load(&s.class_head[c]);
     const unsigned long long end = tail < head + 64 ? tail : head + 64;
     if (end < tail) all = false;
