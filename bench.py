@@ -455,7 +455,8 @@ def run_serving(seconds):
             r = one(mode, rate)
             out["low_load"][f"{mode}_{rate}"] = {k: r.get(k) for k in
                                                  ("lat_p50_ms", "lat_p99_ms",
-                                                  "device_service_p50_p99_ms", "completed",
+                                                  "device_service_p50_p99_ms",
+                                                  "per_class_count_p50_p99_ms", "completed",
                                                   "error") if k in r}
     out["workload"] = ("Poisson 20k req/s (and 500, 5000 req/s), 50/50 detect/precode, "
                        "B in {64,128,256}, U in {8,16,32}, 16/64/256-QAM, 12-1200 subcarriers, "
