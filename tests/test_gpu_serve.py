@@ -140,9 +140,9 @@ def test_same_result_alone_and_in_the_mix(cabi):
 
 
 def test_exact_tracker_requests(cabi):
-    # exact-tracker detection (Eq. 10): up to 16 users on the warp serving kernel,
-    # bitwise equal to the single call; at 32 users on the CTA serving kernel,
-    # checked against the FP64 oracle
+    # exact-tracker detection (Eq. 10) at every padded user count runs on the warp
+    # serving kernel with the single calls' body: bitwise equal to the single call,
+    # and at 32 users also checked against the FP64 oracle
     import oracle
     from tests.parity import check_detect, to_np
     dev = torch.device("cuda:0")
@@ -165,12 +165,11 @@ def test_exact_tracker_requests(cabi):
     finally:
         assert cabi.cg_serve_destroy(srv) == 0
     for r, o in zip(reqs, outs):
-        if r["U"] <= 16:
-            ref = cabi.detect(r["H"], r["inp"], r["N0"], r["K"], r["q"], sinr_mode=1, precision=4)
-            torch.cuda.synchronize()
-            for k in o:
-                assert torch.equal(o[k], ref[k]), f"served exact {k} differs at U={r['U']}"
-        else:
+        ref = cabi.detect(r["H"], r["inp"], r["N0"], r["K"], r["q"], sinr_mode=1, precision=4)
+        torch.cuda.synchronize()
+        for k in o:
+            assert torch.equal(o[k], ref[k]), f"served exact {k} differs at U={r['U']}"
+        if r["U"] > 16:
             ref = oracle.cg_detect(r["H"].cpu().numpy(), r["inp"].cpu().numpy(), r["N0"], 1.0,
                                    r["K"], r["q"], "exact")
             check_detect({k: to_np(v) for k, v in o.items()}, ref)
