@@ -8,6 +8,7 @@
 
 #include "cg_warp.cuh"
 
+
 namespace cgm {
 
 // ---------------------------------------------------------------------------
@@ -492,9 +493,15 @@ __device__ __forceinline__ void serve_poll_host(const ServeArgs& s) {
 // Idle warps that read host memory in each window of 2^kPollWindowShift ns:
 // 1 in kPollSlots. An idle warp sleeps at most kIdleSleepNs between looks,
 // so a request published at low load waits about one window to be seen.
+#ifndef CGM_POLL_SHIFT
+#define CGM_POLL_SHIFT 8
+#endif
+#ifndef CGM_IDLE_SLEEP_NS
+#define CGM_IDLE_SLEEP_NS 128
+#endif
 constexpr int kPollSlots = 128;
-constexpr int kPollWindowShift = 9;
-constexpr unsigned kIdleSleepNs = 512;
+constexpr int kPollWindowShift = CGM_POLL_SHIFT;
+constexpr unsigned kIdleSleepNs = CGM_IDLE_SLEEP_NS;
 
 // Each warp serves its home class (warps are spread evenly over the classes)
 // while that class has work, and otherwise the next class in turn that has
