@@ -44,3 +44,10 @@ def test_kernel_sources_exist():
     csrc = os.path.join(bench.ROOT, "paper_1404_0424_gb300", "csrc")
     for fn in bench.KERNEL_SOURCES:
         assert os.path.exists(os.path.join(csrc, fn)), fn
+
+
+def test_every_precision_has_its_dtype_label():
+    # the bench line's dtype names the arithmetic of the precision that ran
+    assert set(bench.DTYPES) == set(bench.PRECISIONS)
+    assert bench.DTYPES["fp32"] == "f32"
+    assert bench.DTYPES["fp16x3"].startswith("f16x3")
