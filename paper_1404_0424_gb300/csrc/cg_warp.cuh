@@ -1665,7 +1665,6 @@ __device__ __forceinline__ int64_t warp_next_early(const S& s, int64_t cur, int6
 // instance CG_STATUS_TIMEOUT and ends the warp's loop.
 template <int UT, int EL, bool X3, class Src, int SOLVER = SOLVE_CG, bool TMA = false>
 __device__ __forceinline__ void detect_warp_body(const Src& src, unsigned char* mine) {
-  constexpr int NB = UT / 8;
   const int warp = threadIdx.x >> 5;
   unsigned char* ring = mine;
   uint2* frag = reinterpret_cast<uint2*>(mine + WarpCfg<UT>::RING_BYTES);
@@ -2002,7 +2001,6 @@ __device__ __forceinline__ bool precode_vec(const PreItem& it) {
 // 16-byte register loads through L1, where the second pass finds part of H.
 template <int UT, int EL, bool X3, class Src, int SOLVER = SOLVE_CG>
 __device__ __forceinline__ void precode_warp_body(const Src& src, unsigned char* mine) {
-  constexpr int NB = UT / 8;
   const int warp = threadIdx.x >> 5;
   uint2* frag = reinterpret_cast<uint2*>(mine);
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
